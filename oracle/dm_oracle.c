@@ -1,0 +1,629 @@
+/*
+ * CPU oracle for the discrete-continuous dense stereo method of
+ * Shekhovtsov, Reinbacher, Graber, Pock, "Solving Dense Image Matching in
+ * Real-Time using Discrete-Continuous Optimization" (arXiv 1601.06274).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this library.  The product (the CUDA
+ * library) never links, calls or reads anything in this directory, and this
+ * file shares no code, header, table or constant with it.
+ *
+ * The oracle is deliberately plain and slow:
+ *   - the discrete stage runs in int64 with O(K^2) explicit message
+ *     minimisation and the hierarchical minorant as a plain recursion that
+ *     recomputes every message it needs (no reuse, no normalisation);
+ *   - the continuous stage runs in double precision, one formula per line.
+ *
+ * Readings of points the paper leaves open (each is also listed with its
+ * justification in the design notes of the repository):
+ *   R1  census window w x w (default 5), bit = [I(neighbour) < I(centre)],
+ *       clamp-to-edge borders;  cost = popcount(cL(x) ^ cR(x - l)), and
+ *       w*w - 1 when x - l < 0.
+ *   R2  label l <-> disparity l pixels.
+ *   R3  edge weight omega = w_hi if |I1(i) - I1(j)| < T else w_lo.
+ *   R4  the discrete pairwise term is omega * r(|x_i - x_j|) with r of Eq.
+ *       (r-decompose) sampled at integers (must be integer valued).
+ *   R5  Dual MM starts from the zero minorant of the vertical chains, puts the
+ *       whole data cost in the horizontal chains, and one iteration is a
+ *       horizontal pass followed by a vertical pass.
+ *   R6  hierarchical minorant: left part of a split has ceil(n/2) nodes; the
+ *       "half" of the min-marginal in the Handshake is floor(m/2) (toward
+ *       minus infinity); singletons take their whole min-marginal.
+ *   R7  output labelling = per-pixel argmin of lam_h + lam_v (ties -> the
+ *       smallest label); lower bound = sum_i min_l (lam_h + lam_v)_i(l).
+ *   R8  continuous data term D_i = piecewise-linear interpolation of the
+ *       cost samples, with the argument clamped to [0, L-1].
+ *   R9  linearisation slopes s1 = (D(u0) - D(u0-h))/h (left),
+ *       s2 = (D(u0+h) - D(u0))/h (right), both := mean if s2 < s1;
+ *       box [u0-h, u0+h] intersected with [0, L-1].
+ *   R10 data prox middle case returns u0 (the kink), then clamps to the box.
+ *   R11 conjugate (omega r_{a,b})*(s) = b * max(0, |s| - omega a) for
+ *       |s| <= omega, +inf otherwise; prox of Eq. (pprox) with step sigma.
+ *   R12 u0 = labels, p = q = 0; the (u, q) step uses the old (u, p, q); the
+ *       p step uses the extrapolation 2u+ - u; iterations are split evenly over
+ *       the warps (earlier warps take the remainder).
+ */
+
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef int64_t i64;
+
+#define OR_OK 0
+#define OR_ERR_ARG 1
+#define OR_ERR_NONINTEGER 2
+
+/* ------------------------------------------------------------------------ */
+/* Census transform and matching cost (Sec. 3.1: census on a small patch,    */
+/* pixel-wise Hamming distance; Sec. 1: the cost is precomputed for every     */
+/* label).                                                                    */
+/* ------------------------------------------------------------------------ */
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* census bit k (k = 0, 1, ...) is the k-th window neighbour in raster order,
+ * centre skipped: bit = I(neighbour) < I(centre) (reading R1) */
+int or_census(int H, int W, const uint8_t* img, int win, uint32_t* out)
+{
+    if (H <= 0 || W <= 0 || (win != 3 && win != 5)) return OR_ERR_ARG;
+    int r = win / 2;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            uint32_t code = 0;
+            int bit = 0;
+            int centre = img[y * W + x];
+            for (int dy = -r; dy <= r; ++dy)
+                for (int dx = -r; dx <= r; ++dx) {
+                    if (dy == 0 && dx == 0) continue;
+                    int yy = clampi(y + dy, 0, H - 1), xx = clampi(x + dx, 0, W - 1);
+                    if (img[yy * W + xx] < centre) code |= (1u << bit);
+                    ++bit;
+                }
+            out[y * W + x] = code;
+        }
+    return OR_OK;
+}
+
+static int popcount32(uint32_t v)
+{
+    int c = 0;
+    while (v) { c += (int)(v & 1u); v >>= 1; }
+    return c;
+}
+
+/* c[y][x][l] = Hamming(cL[y][x], cR[y][x-l]), or maxc if x - l < 0 (R1, R2) */
+int or_cost_volume(int H, int W, int L, const uint32_t* cl, const uint32_t* cr, int maxc,
+                   int32_t* cost)
+{
+    if (H <= 0 || W <= 0 || L <= 0) return OR_ERR_ARG;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            for (int l = 0; l < L; ++l) {
+                int32_t v = maxc;
+                if (x - l >= 0) v = popcount32(cl[y * W + x] ^ cr[y * W + x - l]);
+                cost[((i64)y * W + x) * L + l] = v;
+            }
+    return OR_OK;
+}
+
+/* Edge strengths omega_ij (Sec. 2.1: image dependent, smaller across sharp
+ * edges; reading R3).  wh[y][x] is the edge (y,x)-(y,x+1), wv[y][x] the edge
+ * (y,x)-(y+1,x); entries without an edge are 0. */
+int or_edge_weights(int H, int W, const uint8_t* img, int T, int w_hi, int w_lo,
+                    int32_t* wh, int32_t* wv)
+{
+    if (H <= 0 || W <= 0) return OR_ERR_ARG;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int i = y * W + x;
+            wh[i] = 0;
+            wv[i] = 0;
+            if (x + 1 < W) wh[i] = abs((int)img[i] - (int)img[i + 1]) < T ? w_hi : w_lo;
+            if (y + 1 < H) wv[i] = abs((int)img[i] - (int)img[i + W]) < T ? w_hi : w_lo;
+        }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Penalty r (Eq. r-decompose): r = r_{eps,delta} - r_{0, C + delta - eps     */
+/* delta}, r_{a,b}(t) = a|t| if |t| <= b else |t| - b(1-a).                   */
+/* ------------------------------------------------------------------------ */
+
+double or_r_ab(double t, double a, double b)
+{
+    double at = fabs(t);
+    return at <= b ? a * at : at - b * (1.0 - a);
+}
+
+double or_r(double t, double eps, double delta, double C)
+{
+    return or_r_ab(t, eps, delta) - or_r_ab(t, 0.0, C + delta - eps * delta);
+}
+
+/* V[t] = omega * r(t), t = 0..K-1, sampled at integer label distances
+ * (Sec. 2.2: f_ij = omega_ij r((Au(x))_ij); Fig. 2).  Fails if not integer. */
+int or_penalty_table(int omega, double eps, double delta, double C, int K, i64* V)
+{
+    for (int t = 0; t < K; ++t) {
+        double v = (double)omega * or_r((double)t, eps, delta, C);
+        double rv = nearbyint(v);
+        if (fabs(v - rv) > 1e-9) return OR_ERR_NONINTEGER;
+        V[t] = (i64)rv;
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Message passing (App. A, Eq. msg-pass; procedure Msg of Alg. Handshake):  */
+/*   out(x') = min_x [ a(x) + f_ij(x, x') ],  f_ij(x, x') = V[|x - x'|].      */
+/* ------------------------------------------------------------------------ */
+
+void or_msg(int K, const i64* a, const i64* V, i64* out)
+{
+    for (int xp = 0; xp < K; ++xp) {
+        i64 best = INT64_MAX;
+        for (int x = 0; x < K; ++x) {
+            i64 v = a[x] + V[x > xp ? x - xp : xp - x];
+            if (v < best) best = v;
+        }
+        out[xp] = best;
+    }
+}
+
+/* Min-marginals of a chain (App. A, Eq. min-marg-expression): left messages
+ * phi_{i-1,i}, right messages phi_{i+1,i}, m_i = f_i + phi_{i-1,i} + phi_{i+1,i}.
+ * theta: n*K unaries; V: (n-1)*K tables, row k for the edge (k, k+1). */
+void or_min_marginals(int n, int K, const i64* theta, const i64* V, i64* mm)
+{
+    i64* left = (i64*)calloc((size_t)n * K, sizeof(i64));
+    i64* right = (i64*)calloc((size_t)n * K, sizeof(i64));
+    i64* tmp = (i64*)malloc((size_t)K * sizeof(i64));
+    for (int k = 1; k < n; ++k) {
+        for (int l = 0; l < K; ++l) tmp[l] = left[(i64)(k - 1) * K + l] + theta[(i64)(k - 1) * K + l];
+        or_msg(K, tmp, V + (i64)(k - 1) * K, left + (i64)k * K);
+    }
+    for (int k = n - 2; k >= 0; --k) {
+        for (int l = 0; l < K; ++l) tmp[l] = right[(i64)(k + 1) * K + l] + theta[(i64)(k + 1) * K + l];
+        or_msg(K, tmp, V + (i64)k * K, right + (i64)k * K);
+    }
+    for (i64 e = 0; e < (i64)n * K; ++e) mm[e] = theta[e] + left[e] + right[e];
+    free(left);
+    free(right);
+    free(tmp);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hierarchical minorant (App. A "Hierarchical Minorants", Alg. Handshake).  */
+/* rec(a, b, Lin, Rin): the sub-chain a..b with the message Lin entering a    */
+/* from the left and Rin entering b from the right.                           */
+/* ------------------------------------------------------------------------ */
+
+static i64 floor_half(i64 m) { return m >= 0 ? m / 2 : -((-m + 1) / 2); }
+
+static void hier_rec(int a, int b, int K, const i64* theta, const i64* V, const i64* Lin,
+                     const i64* Rin, i64* lam)
+{
+    if (a == b) {
+        /* a single node keeps its whole min-marginal (reading R6) */
+        for (int l = 0; l < K; ++l) lam[(i64)a * K + l] = theta[(i64)a * K + l] + Lin[l] + Rin[l];
+        return;
+    }
+    int len = b - a + 1;
+    int i = a + (len + 1) / 2 - 1; /* left part keeps ceil(len/2) nodes */
+    int j = i + 1;
+    i64* Lm = (i64*)malloc((size_t)K * sizeof(i64));
+    i64* Rm = (i64*)malloc((size_t)K * sizeof(i64));
+    i64* tmp = (i64*)malloc((size_t)K * sizeof(i64));
+    i64* phi_ji = (i64*)malloc((size_t)K * sizeof(i64));
+    i64* phi_ij = (i64*)malloc((size_t)K * sizeof(i64));
+    i64* m_i = (i64*)malloc((size_t)K * sizeof(i64));
+
+    /* left min-marginal message into i: sweep a .. i-1 */
+    memcpy(Lm, Lin, (size_t)K * sizeof(i64));
+    for (int k = a; k < i; ++k) {
+        for (int l = 0; l < K; ++l) tmp[l] = theta[(i64)k * K + l] + Lm[l];
+        or_msg(K, tmp, V + (i64)k * K, Lm);
+    }
+    /* right min-marginal message into j: sweep b .. j+1 */
+    memcpy(Rm, Rin, (size_t)K * sizeof(i64));
+    for (int k = b; k > j; --k) {
+        for (int l = 0; l < K; ++l) tmp[l] = theta[(i64)k * K + l] + Rm[l];
+        or_msg(K, tmp, V + (i64)(k - 1) * K, Rm);
+    }
+    /* Handshake over the edge (i, j) */
+    for (int l = 0; l < K; ++l) tmp[l] = theta[(i64)j * K + l] + Rm[l];
+    or_msg(K, tmp, V + (i64)i * K, phi_ji);                  /* message j -> i        */
+    for (int l = 0; l < K; ++l)
+        m_i[l] = Lm[l] + theta[(i64)i * K + l] + phi_ji[l];  /* total min-marginal at i */
+    for (int l = 0; l < K; ++l) tmp[l] = floor_half(m_i[l]) - phi_ji[l];
+    or_msg(K, tmp, V + (i64)i * K, phi_ij);                  /* share a half to the right */
+    for (int l = 0; l < K; ++l) tmp[l] = -phi_ij[l];
+    or_msg(K, tmp, V + (i64)i * K, phi_ji);                  /* bounce back the rest   */
+
+    hier_rec(a, i, K, theta, V, Lin, phi_ji, lam);
+    hier_rec(j, b, K, theta, V, phi_ij, Rin, lam);
+    free(Lm); free(Rm); free(tmp); free(phi_ji); free(phi_ij); free(m_i);
+}
+
+/* lam = hierarchical minorant of the chain (theta, V) with zero boundary messages */
+void or_hier_minorant(int n, int K, const i64* theta, const i64* V, i64* lam)
+{
+    i64* zero = (i64*)calloc((size_t)K, sizeof(i64));
+    hier_rec(0, n - 1, K, theta, V, zero, zero, lam);
+    free(zero);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dual MM (Alg. Dual_MM) on the 4-connected grid split into horizontal      */
+/* chains f (data cost + horizontal edges) and vertical chains g (vertical    */
+/* edges only).  lam_h is the minorant f^{k+1} of f, lam_v the minorant g^k.  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int ntab;          /* distinct omegas */
+    int omega[8];
+    i64* table[8];     /* K entries each */
+} or_tables;
+
+static int build_tables(or_tables* T, int K, const int32_t* w, int count, double eps,
+                        double delta, double C)
+{
+    T->ntab = 0;
+    for (int e = 0; e < count; ++e) {
+        int om = w[e];
+        int found = 0;
+        for (int t = 0; t < T->ntab; ++t) if (T->omega[t] == om) found = 1;
+        if (found) continue;
+        if (T->ntab == 8) return OR_ERR_ARG;
+        T->omega[T->ntab] = om;
+        T->table[T->ntab] = (i64*)malloc((size_t)K * sizeof(i64));
+        int rc = or_penalty_table(om, eps, delta, C, K, T->table[T->ntab]);
+        if (rc) return rc;
+        T->ntab++;
+    }
+    return OR_OK;
+}
+
+static const i64* find_table(const or_tables* T, int om)
+{
+    for (int t = 0; t < T->ntab; ++t) if (T->omega[t] == om) return T->table[t];
+    return NULL;
+}
+
+static void free_tables(or_tables* T)
+{
+    for (int t = 0; t < T->ntab; ++t) free(T->table[t]);
+    T->ntab = 0;
+}
+
+/* One pass of Alg. Dual_MM.
+ *   which = 0 (horizontal): theta = cost + lam_in (lam_in = lam_v),
+ *             mu = hier(theta), lam_out = mu - lam_in   (steps 1-2)
+ *   which = 1 (vertical):   theta = lam_in (lam_in = lam_h),
+ *             nu = hier(theta), lam_out = nu - lam_in   (steps 3-4)     */
+int or_dmm_pass(int H, int W, int L, const int32_t* cost, const int32_t* wh,
+                const int32_t* wv, double eps, double delta, double C, int which,
+                const i64* lam_in, i64* lam_out, int nthreads)
+{
+    if (H <= 0 || W <= 0 || L <= 0 || (which != 0 && which != 1)) return OR_ERR_ARG;
+    or_tables T;
+    int rc = build_tables(&T, L, which == 0 ? wh : wv, H * W, eps, delta, C);
+    if (rc) { free_tables(&T); return rc; }
+    int nchains = which == 0 ? H : W;
+    int n = which == 0 ? W : H;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int c = 0; c < nchains; ++c) {
+        i64* theta = (i64*)malloc((size_t)n * L * sizeof(i64));
+        i64* V = (i64*)malloc((size_t)(n > 1 ? n - 1 : 1) * L * sizeof(i64));
+        i64* mu = (i64*)malloc((size_t)n * L * sizeof(i64));
+        for (int k = 0; k < n; ++k) {
+            int y = which == 0 ? c : k, x = which == 0 ? k : c;
+            i64 pix = (i64)y * W + x;
+            for (int l = 0; l < L; ++l) {
+                i64 t = lam_in[pix * L + l];
+                if (which == 0) t += cost[pix * L + l];
+                theta[(i64)k * L + l] = t;
+            }
+            if (k + 1 < n) {
+                const i64* tab = find_table(&T, which == 0 ? wh[pix] : wv[pix]);
+                memcpy(V + (i64)k * L, tab, (size_t)L * sizeof(i64));
+            }
+        }
+        or_hier_minorant(n, L, theta, V, mu);
+        for (int k = 0; k < n; ++k) {
+            int y = which == 0 ? c : k, x = which == 0 ? k : c;
+            i64 pix = (i64)y * W + x;
+            for (int l = 0; l < L; ++l)
+                lam_out[pix * L + l] = mu[(i64)k * L + l] - lam_in[pix * L + l];
+        }
+        free(theta); free(V); free(mu);
+    }
+    free_tables(&T);
+    return OR_OK;
+}
+
+/* Labels and lower bound from the two minorants (weak duality, Eq. DD-dual;
+ * readings R7). */
+i64 or_dmm_outputs(int H, int W, int L, const i64* lam_h, const i64* lam_v, uint16_t* labels)
+{
+    i64 lb = 0;
+    for (i64 p = 0; p < (i64)H * W; ++p) {
+        i64 best = INT64_MAX;
+        int arg = 0;
+        for (int l = 0; l < L; ++l) {
+            i64 v = lam_h[p * L + l] + lam_v[p * L + l];
+            if (v < best) { best = v; arg = l; }
+        }
+        lb += best;
+        if (labels) labels[p] = (uint16_t)arg;
+    }
+    return lb;
+}
+
+/* Full Dual MM: iters x (horizontal pass, vertical pass), starting from the
+ * given lam_v (zero for a cold start).  lb[t] is the bound after iteration t. */
+int or_dmm(int H, int W, int L, const int32_t* cost, const int32_t* wh, const int32_t* wv,
+           double eps, double delta, double C, int iters, i64* lam_h, i64* lam_v, i64* lb,
+           uint16_t* labels, int nthreads)
+{
+    for (int t = 0; t < iters; ++t) {
+        int rc = or_dmm_pass(H, W, L, cost, wh, wv, eps, delta, C, 0, lam_v, lam_h, nthreads);
+        if (rc) return rc;
+        rc = or_dmm_pass(H, W, L, cost, wh, wv, eps, delta, C, 1, lam_h, lam_v, nthreads);
+        if (rc) return rc;
+        i64 b = or_dmm_outputs(H, W, L, lam_h, lam_v, (t == iters - 1) ? labels : NULL);
+        if (lb) lb[t] = b;
+    }
+    return OR_OK;
+}
+
+/* Discrete energy, Eq. (energy-pairwise) with the stereo terms of Sec. 2.2. */
+i64 or_discrete_energy(int H, int W, int L, const int32_t* cost, const int32_t* wh,
+                       const int32_t* wv, double eps, double delta, double C,
+                       const uint16_t* labels)
+{
+    i64 e = 0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            i64 p = (i64)y * W + x;
+            int xi = labels[p];
+            e += cost[p * L + xi];
+            if (x + 1 < W)
+                e += (i64)nearbyint(wh[p] * or_r((double)(xi - labels[p + 1]), eps, delta, C));
+            if (y + 1 < H)
+                e += (i64)nearbyint(wv[p] * or_r((double)(xi - labels[p + W]), eps, delta, C));
+        }
+    return e;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Continuous refinement (Sec. 2.4 and 3.1), double precision.               */
+/* ------------------------------------------------------------------------ */
+
+/* D_i(u): piecewise-linear interpolation of the samples c[0..L-1] (reading R8) */
+double or_interp(int L, const double* c, double u)
+{
+    if (u <= 0.0) return c[0];
+    if (u >= (double)(L - 1)) return c[L - 1];
+    double fl = floor(u);
+    int k = (int)fl;
+    double t = u - fl;
+    return c[k] + t * (c[k + 1] - c[k]);
+}
+
+/* Linearisation of the data term around u0 (Sec. 3.1; readings R9):
+ * slopes s1 (left of u0), s2 (right of u0), box [lo, hi]. */
+void or_linearise_px(int L, const double* c, double alpha, double u0, double h, double* s1,
+                     double* s2, double* lo, double* hi)
+{
+    double d0 = or_interp(L, c, u0);
+    double dm = or_interp(L, c, u0 - h);
+    double dp = or_interp(L, c, u0 + h);
+    double a = alpha * (d0 - dm) / h;
+    double b = alpha * (dp - d0) / h;
+    if (b < a) { a = 0.5 * (a + b); b = a; }
+    *s1 = a;
+    *s2 = b;
+    *lo = u0 - h > 0.0 ? u0 - h : 0.0;
+    *hi = u0 + h < (double)(L - 1) ? u0 + h : (double)(L - 1);
+}
+
+/* prox of tau * D~ at uh (Sec. 3.1, pointwise soft-threshold; reading R10) */
+double or_prox_data(double uh, double u0, double s1, double s2, double lo, double hi,
+                    double tau)
+{
+    double v;
+    if (uh > u0 + tau * s2) v = uh - tau * s2;
+    else if (uh < u0 + tau * s1) v = uh - tau * s1;
+    else v = u0;
+    if (v < lo) v = lo;
+    if (v > hi) v = hi;
+    return v;
+}
+
+/* prox of step * (omega r_{a,b})* at t (Eq. pprox; reading R11):
+ * t' = t if |t| <= a*omega, else sign(t) max(a*omega, |t| - b*step); clamp to +-omega */
+double or_prox_conj(double t, double omega, double a, double b, double step)
+{
+    double tp;
+    if (fabs(t) <= a * omega) tp = t;
+    else {
+        double m = fabs(t) - b * step;
+        if (m < a * omega) m = a * omega;
+        tp = t > 0 ? m : -m;
+    }
+    if (tp > omega) tp = omega;
+    if (tp < -omega) tp = -omega;
+    return tp;
+}
+
+/* convex conjugate (omega r_{a,b})*(s) (reading R11); +inf outside |s| <= omega */
+double or_conj(double s, double omega, double a, double b)
+{
+    if (fabs(s) > omega * (1.0 + 1e-12)) return INFINITY;
+    double v = fabs(s) - omega * a;
+    return v > 0 ? b * v : 0.0;
+}
+
+typedef struct {
+    double eps, delta, C;   /* penalty r */
+    double lambda_r;        /* regulariser weight (multiplies omega) */
+    double tau, sigma, h;   /* primal / dual steps, linearisation half-width */
+    int warps;              /* re-linearisations (warping) */
+} or_cont_params;
+
+/* Continuous energy E(u) = sum_i alpha_i D_i(u_i) + sum_e lambda_r omega_e r((Au)_e)
+ * (Eq. mrf_formulation, regularizer-form). */
+double or_cont_energy(int H, int W, int L, const double* cost, const double* alpha,
+                      const double* wh, const double* wv, const or_cont_params* P,
+                      const double* u)
+{
+    double e = 0.0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            i64 p = (i64)y * W + x;
+            double a = alpha ? alpha[p] : 1.0;
+            e += a * or_interp(L, cost + p * L, u[p]);
+            if (x + 1 < W) e += P->lambda_r * wh[p] * or_r(u[p] - u[p + 1], P->eps, P->delta, P->C);
+            if (y + 1 < H) e += P->lambda_r * wv[p] * or_r(u[p] - u[p + W], P->eps, P->delta, P->C);
+        }
+    return e;
+}
+
+/* Non-linear primal-dual refinement (Eq. cont_iterates with the operator of
+ * Eq. cont_problem, nabla A of Sec. 2.4, data term of Sec. 3.1).
+ *   A u on the edge e = (i, j) (i left/top, j right/bottom) is u_i - u_j.
+ *   u  <- prox_{tau D~}(u - tau A^T (p - q))
+ *   q  <- prox_{tau R-*}(q + tau A u_old)
+ *   p  <- prox_{sigma R+*}(p + sigma A (2 u_new - u_old))
+ * with R+ = sum lambda_r omega r_{eps,delta}, R- = sum lambda_r omega r_{0,C+delta-eps delta}.
+ * State arrays are H*W (edge arrays store the edge at its left/top pixel; the
+ * last column of *_h and last row of *_v are unused and kept at 0).
+ * If init is nonzero, p and q are reset to 0 first; u holds u0 on entry.
+ * energy (nullable): E(u) after each warp. */
+int or_refine(int H, int W, int L, const double* cost, const double* alpha, const double* wh,
+              const double* wv, int iters, const or_cont_params* P, double* u, double* ph,
+              double* pv, double* qh, double* qv, int init, double* energy)
+{
+    if (H <= 0 || W <= 0 || L < 2 || P->warps <= 0) return OR_ERR_ARG;
+    i64 N = (i64)H * W;
+    double* s1 = (double*)malloc(N * sizeof(double));
+    double* s2 = (double*)malloc(N * sizeof(double));
+    double* lo = (double*)malloc(N * sizeof(double));
+    double* hi = (double*)malloc(N * sizeof(double));
+    double* u0 = (double*)malloc(N * sizeof(double));
+    double* un = (double*)malloc(N * sizeof(double));
+    if (init) {
+        for (i64 p = 0; p < N; ++p) ph[p] = pv[p] = qh[p] = qv[p] = 0.0;
+    }
+    const double bp = P->delta;                              /* beta of R+ */
+    const double ap = P->eps;                                /* alpha of R+ */
+    const double bq = P->C + P->delta - P->eps * P->delta;   /* beta of R- (alpha = 0) */
+    const double tau = P->tau, sigma = P->sigma;
+    int base = iters / P->warps, extra = iters % P->warps;
+    for (int w = 0; w < P->warps; ++w) {
+        int nit = base + (w < extra ? 1 : 0);
+        for (i64 p = 0; p < N; ++p) {
+            u0[p] = u[p];
+            or_linearise_px(L, cost + p * L, alpha ? alpha[p] : 1.0, u0[p], P->h, &s1[p], &s2[p],
+                            &lo[p], &hi[p]);
+        }
+        for (int it = 0; it < nit; ++it) {
+            /* primal step for u (uses old p, q) */
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    i64 p = (i64)y * W + x;
+                    double div = 0.0; /* (A^T (p - q))_i */
+                    if (x + 1 < W) div += ph[p] - qh[p];
+                    if (x > 0) div -= ph[p - 1] - qh[p - 1];
+                    if (y + 1 < H) div += pv[p] - qv[p];
+                    if (y > 0) div -= pv[p - W] - qv[p - W];
+                    un[p] = or_prox_data(u[p] - tau * div, u0[p], s1[p], s2[p], lo[p], hi[p], tau);
+                }
+            /* primal step for q (uses old u) and dual step for p (extrapolated u) */
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    i64 p = (i64)y * W + x;
+                    if (x + 1 < W) {
+                        double om = P->lambda_r * wh[p];
+                        double au = u[p] - u[p + 1];
+                        double ext = (2.0 * un[p] - u[p]) - (2.0 * un[p + 1] - u[p + 1]);
+                        qh[p] = or_prox_conj(qh[p] + tau * au, om, 0.0, bq, tau);
+                        ph[p] = or_prox_conj(ph[p] + sigma * ext, om, ap, bp, sigma);
+                    }
+                    if (y + 1 < H) {
+                        double om = P->lambda_r * wv[p];
+                        double au = u[p] - u[p + W];
+                        double ext = (2.0 * un[p] - u[p]) - (2.0 * un[p + W] - u[p + W]);
+                        qv[p] = or_prox_conj(qv[p] + tau * au, om, 0.0, bq, tau);
+                        pv[p] = or_prox_conj(pv[p] + sigma * ext, om, ap, bp, sigma);
+                    }
+                }
+            memcpy(u, un, N * sizeof(double));
+        }
+        if (energy) energy[w] = or_cont_energy(H, W, L, cost, alpha, wh, wv, P, u);
+    }
+    free(s1); free(s2); free(lo); free(hi); free(u0); free(un);
+    return OR_OK;
+}
+
+/* Primal and dual objective of the convex problem obtained when R- vanishes
+ * (C -> infinity) for a fixed linearisation (used to check that the
+ * primal-dual gap closes).  primal = sum D~_i(u_i) + sum lambda_r omega r_{eps,delta}(Au);
+ * dual = -sum D~_i*(-(A^T p)_i) - sum (lambda_r omega r_{eps,delta})*(p).
+ * D~_i* is the max over the vertices {lo, u0, hi} of s v - D~_i(v). */
+void or_convex_gap(int H, int W, int L, const double* cost, const double* alpha,
+                   const double* wh, const double* wv, const or_cont_params* P,
+                   const double* u0in, const double* u, const double* ph, const double* pv,
+                   double* primal, double* dual)
+{
+    double pr = 0.0, du = 0.0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            i64 p = (i64)y * W + x;
+            double s1, s2, lo, hi;
+            double a = alpha ? alpha[p] : 1.0;
+            or_linearise_px(L, cost + p * L, a, u0in[p], P->h, &s1, &s2, &lo, &hi);
+            double d0 = a * or_interp(L, cost + p * L, u0in[p]);
+            /* D~(v) = d0 + s1 (v - u0) for v <= u0, s2 (v - u0) above, +inf outside [lo, hi] */
+            double v = u[p];
+            double dt = v <= u0in[p] ? d0 + s1 * (v - u0in[p]) : d0 + s2 * (v - u0in[p]);
+            if (v < lo - 1e-12 || v > hi + 1e-12) dt = INFINITY;
+            pr += dt;
+            double atp = 0.0;
+            if (x + 1 < W) atp += ph[p];
+            if (x > 0) atp -= ph[p - 1];
+            if (y + 1 < H) atp += pv[p];
+            if (y > 0) atp -= pv[p - W];
+            double s = -atp;
+            double verts[3] = {lo, u0in[p], hi};
+            double best = -INFINITY;
+            for (int k = 0; k < 3; ++k) {
+                double vv = verts[k];
+                double dv = vv <= u0in[p] ? d0 + s1 * (vv - u0in[p]) : d0 + s2 * (vv - u0in[p]);
+                double val = s * vv - dv;
+                if (val > best) best = val;
+            }
+            du -= best;
+            if (x + 1 < W) {
+                double om = P->lambda_r * wh[p];
+                pr += om * or_r_ab(u[p] - u[p + 1], P->eps, P->delta);
+                du -= or_conj(ph[p], om, P->eps, P->delta);
+            }
+            if (y + 1 < H) {
+                double om = P->lambda_r * wv[p];
+                pr += om * or_r_ab(u[p] - u[p + W], P->eps, P->delta);
+                du -= or_conj(pv[p], om, P->eps, P->delta);
+            }
+        }
+    *primal = pr;
+    *dual = du;
+}

@@ -1,0 +1,329 @@
+"""Python front end of the CPU oracle (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg import
+this module.  It compiles ``dm_oracle.c`` with gcc into ``_build/`` next to
+this file and exposes numpy-level wrappers.  Nothing here touches the CUDA
+library or the package that wraps it.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libdm_oracle.so")
+_lib = None
+
+i64p = ctypes.POINTER(ctypes.c_int64)
+i32p = ctypes.POINTER(ctypes.c_int32)
+u32p = ctypes.POINTER(ctypes.c_uint32)
+u16p = ctypes.POINTER(ctypes.c_uint16)
+u8p = ctypes.POINTER(ctypes.c_uint8)
+f64p = ctypes.POINTER(ctypes.c_double)
+
+
+class ContParams(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("delta", ctypes.c_double), ("C", ctypes.c_double),
+                ("lambda_r", ctypes.c_double), ("tau", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("h", ctypes.c_double), ("warps", ctypes.c_int)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc -O2, OpenMP) into oracle/_build/."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        L = _lib
+        L.or_census.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int, u32p]
+        L.or_cost_volume.argtypes = [ctypes.c_int] * 3 + [u32p, u32p, ctypes.c_int, i32p]
+        L.or_edge_weights.argtypes = [ctypes.c_int, ctypes.c_int, u8p] + [ctypes.c_int] * 3 + [i32p, i32p]
+        L.or_r.argtypes = [ctypes.c_double] * 4
+        L.or_r.restype = ctypes.c_double
+        L.or_r_ab.argtypes = [ctypes.c_double] * 3
+        L.or_r_ab.restype = ctypes.c_double
+        L.or_penalty_table.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int, i64p]
+        L.or_msg.argtypes = [ctypes.c_int, i64p, i64p, i64p]
+        L.or_min_marginals.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
+        L.or_hier_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
+        L.or_dmm_pass.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
+                                  + [ctypes.c_int, i64p, i64p, ctypes.c_int])
+        L.or_dmm_outputs.argtypes = [ctypes.c_int] * 3 + [i64p, i64p, u16p]
+        L.or_dmm_outputs.restype = ctypes.c_int64
+        L.or_dmm.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
+                             + [ctypes.c_int, i64p, i64p, i64p, u16p, ctypes.c_int])
+        L.or_discrete_energy.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p]
+                                         + [ctypes.c_double] * 3 + [u16p])
+        L.or_discrete_energy.restype = ctypes.c_int64
+        L.or_interp.argtypes = [ctypes.c_int, f64p, ctypes.c_double]
+        L.or_interp.restype = ctypes.c_double
+        L.or_linearise_px.argtypes = [ctypes.c_int, f64p] + [ctypes.c_double] * 3 + [f64p] * 4
+        L.or_prox_data.argtypes = [ctypes.c_double] * 7
+        L.or_prox_data.restype = ctypes.c_double
+        L.or_prox_conj.argtypes = [ctypes.c_double] * 5
+        L.or_prox_conj.restype = ctypes.c_double
+        L.or_conj.argtypes = [ctypes.c_double] * 4
+        L.or_conj.restype = ctypes.c_double
+        L.or_cont_energy.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4
+                                     + [ctypes.POINTER(ContParams), f64p])
+        L.or_cont_energy.restype = ctypes.c_double
+        L.or_refine.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4 + [ctypes.c_int,
+                                ctypes.POINTER(ContParams)] + [f64p] * 5 + [ctypes.c_int, f64p])
+        L.or_convex_gap.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4
+                                    + [ctypes.POINTER(ContParams)] + [f64p] * 4 + [f64p, f64p])
+    return _lib
+
+
+def _p(a: np.ndarray, t):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(t)
+
+
+def _chk(rc: int, what: str):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+# ---------------------------------------------------------------------------
+# Parameters (the readings of the paper; see the C file header)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Params:
+    census_win: int = 5
+    edge_T: int = 16
+    w_hi: int = 8
+    w_lo: int = 4
+    eps: float = 0.25
+    delta: float = 1.0
+    C: float = 2.0
+    lambda_r: float = 1.0
+    alpha: float = 1.0
+    tau: float = 0.35
+    sigma: float = 0.35
+    h: float = 1.0
+    warps: int = 5
+
+    def cont(self) -> ContParams:
+        return ContParams(self.eps, self.delta, self.C, self.lambda_r, self.tau, self.sigma,
+                          self.h, self.warps)
+
+
+# ---------------------------------------------------------------------------
+# Wrappers
+# ---------------------------------------------------------------------------
+
+def census(img: np.ndarray, win: int = 5) -> np.ndarray:
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape
+    out = np.zeros((H, W), dtype=np.uint32)
+    _chk(lib().or_census(H, W, _p(img, u8p), win, _p(out, u32p)), "census")
+    return out
+
+
+def cost_volume(left: np.ndarray, right: np.ndarray, L: int, win: int = 5) -> np.ndarray:
+    cl, cr = census(left, win), census(right, win)
+    H, W = cl.shape
+    out = np.zeros((H, W, L), dtype=np.int32)
+    _chk(lib().or_cost_volume(H, W, L, _p(cl, u32p), _p(cr, u32p), win * win - 1,
+                              _p(out, i32p)), "cost_volume")
+    return out
+
+
+def edge_weights(img: np.ndarray, P: Params = Params()):
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape
+    wh = np.zeros((H, W), dtype=np.int32)
+    wv = np.zeros((H, W), dtype=np.int32)
+    _chk(lib().or_edge_weights(H, W, _p(img, u8p), P.edge_T, P.w_hi, P.w_lo, _p(wh, i32p),
+                               _p(wv, i32p)), "edge_weights")
+    return wh, wv
+
+
+def r(t: float, P: Params = Params()) -> float:
+    return lib().or_r(float(t), P.eps, P.delta, P.C)
+
+
+def penalty_table(omega: int, K: int, P: Params = Params()) -> np.ndarray:
+    V = np.zeros(K, dtype=np.int64)
+    _chk(lib().or_penalty_table(int(omega), P.eps, P.delta, P.C, K, _p(V, i64p)), "penalty_table")
+    return V
+
+
+def msg(a: np.ndarray, V: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    V = np.ascontiguousarray(V, dtype=np.int64)
+    out = np.zeros_like(a)
+    lib().or_msg(len(a), _p(a, i64p), _p(V, i64p), _p(out, i64p))
+    return out
+
+
+def min_marginals(theta: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """theta: [n, K]; V: [n-1, K] (table of edge k, k+1)."""
+    theta = np.ascontiguousarray(theta, dtype=np.int64)
+    n, K = theta.shape
+    V = np.ascontiguousarray(V, dtype=np.int64).reshape(max(n - 1, 1), K) if n > 1 else np.zeros((1, K), np.int64)
+    out = np.zeros_like(theta)
+    lib().or_min_marginals(n, K, _p(theta, i64p), _p(V, i64p), _p(out, i64p))
+    return out
+
+
+def hier_minorant(theta: np.ndarray, V: np.ndarray) -> np.ndarray:
+    theta = np.ascontiguousarray(theta, dtype=np.int64)
+    n, K = theta.shape
+    V = np.ascontiguousarray(V, dtype=np.int64).reshape(max(n - 1, 1), K) if n > 1 else np.zeros((1, K), np.int64)
+    out = np.zeros_like(theta)
+    lib().or_hier_minorant(n, K, _p(theta, i64p), _p(V, i64p), _p(out, i64p))
+    return out
+
+
+def dmm_pass(cost, wh, wv, which: int, lam_in, P: Params = Params(), nthreads: int = 0):
+    cost = np.ascontiguousarray(cost, dtype=np.int32)
+    H, W, L = cost.shape
+    lam_in = np.ascontiguousarray(lam_in, dtype=np.int64)
+    out = np.zeros((H, W, L), dtype=np.int64)
+    _chk(lib().or_dmm_pass(H, W, L, _p(cost, i32p), _p(np.ascontiguousarray(wh, np.int32), i32p),
+                           _p(np.ascontiguousarray(wv, np.int32), i32p), P.eps, P.delta, P.C,
+                           which, _p(lam_in, i64p), _p(out, i64p), nthreads), "dmm_pass")
+    return out
+
+
+def dmm_outputs(lam_h, lam_v):
+    lam_h = np.ascontiguousarray(lam_h, dtype=np.int64)
+    lam_v = np.ascontiguousarray(lam_v, dtype=np.int64)
+    H, W, L = lam_h.shape
+    labels = np.zeros((H, W), dtype=np.uint16)
+    lb = lib().or_dmm_outputs(H, W, L, _p(lam_h, i64p), _p(lam_v, i64p), _p(labels, u16p))
+    return labels, int(lb)
+
+
+def dmm(cost, wh, wv, iters: int, P: Params = Params(), lam_v0=None, nthreads: int = 0):
+    """Dual MM; returns (labels, lb per iteration, lam_h, lam_v)."""
+    cost = np.ascontiguousarray(cost, dtype=np.int32)
+    H, W, L = cost.shape
+    lam_h = np.zeros((H, W, L), dtype=np.int64)
+    lam_v = np.zeros((H, W, L), dtype=np.int64) if lam_v0 is None else np.array(lam_v0, dtype=np.int64)
+    lb = np.zeros(max(iters, 1), dtype=np.int64)
+    labels = np.zeros((H, W), dtype=np.uint16)
+    _chk(lib().or_dmm(H, W, L, _p(cost, i32p), _p(np.ascontiguousarray(wh, np.int32), i32p),
+                      _p(np.ascontiguousarray(wv, np.int32), i32p), P.eps, P.delta, P.C, iters,
+                      _p(lam_h, i64p), _p(lam_v, i64p), _p(lb, i64p), _p(labels, u16p),
+                      nthreads), "dmm")
+    return labels, lb[:iters], lam_h, lam_v
+
+
+def discrete_energy(cost, wh, wv, labels, P: Params = Params()) -> int:
+    cost = np.ascontiguousarray(cost, dtype=np.int32)
+    H, W, L = cost.shape
+    labels = np.ascontiguousarray(labels, dtype=np.uint16)
+    return int(lib().or_discrete_energy(H, W, L, _p(cost, i32p),
+                                        _p(np.ascontiguousarray(wh, np.int32), i32p),
+                                        _p(np.ascontiguousarray(wv, np.int32), i32p),
+                                        P.eps, P.delta, P.C, _p(labels, u16p)))
+
+
+def interp(c: np.ndarray, u: float) -> float:
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    return lib().or_interp(len(c), _p(c, f64p), float(u))
+
+
+def linearise_px(c, alpha, u0, h):
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    out = [ctypes.c_double() for _ in range(4)]
+    lib().or_linearise_px(len(c), _p(c, f64p), float(alpha), float(u0), float(h),
+                          *[ctypes.byref(o) for o in out])
+    return tuple(o.value for o in out)
+
+
+def prox_data(uh, u0, s1, s2, lo, hi, tau):
+    return lib().or_prox_data(uh, u0, s1, s2, lo, hi, tau)
+
+
+def prox_conj(t, omega, a, b, step):
+    return lib().or_prox_conj(t, omega, a, b, step)
+
+
+def conj(s, omega, a, b):
+    return lib().or_conj(s, omega, a, b)
+
+
+def cont_energy(cost, wh, wv, u, P: Params = Params(), alpha=None) -> float:
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    H, W, L = cost.shape
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    al = None if alpha is None else np.ascontiguousarray(np.broadcast_to(alpha, (H, W)), np.float64)
+    cp = P.cont()
+    return lib().or_cont_energy(H, W, L, _p(cost, f64p), None if al is None else _p(al, f64p),
+                                _p(np.ascontiguousarray(wh, np.float64), f64p),
+                                _p(np.ascontiguousarray(wv, np.float64), f64p),
+                                ctypes.byref(cp), _p(u, f64p))
+
+
+def refine(cost, wh, wv, u0, iters: int, P: Params = Params(), alpha=None, state=None):
+    """Primal-dual refinement; returns (u, (ph, pv, qh, qv), energy per warp)."""
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    H, W, L = cost.shape
+    u = np.array(u0, dtype=np.float64).reshape(H, W).copy()
+    if state is None:
+        ph, pv, qh, qv = (np.zeros((H, W)) for _ in range(4))
+        init = 1
+    else:
+        ph, pv, qh, qv = (np.array(s, dtype=np.float64).copy() for s in state)
+        init = 0
+    al = None if alpha is None else np.ascontiguousarray(np.broadcast_to(alpha, (H, W)), np.float64)
+    energy = np.zeros(P.warps)
+    cp = P.cont()
+    _chk(lib().or_refine(H, W, L, _p(cost, f64p), None if al is None else _p(al, f64p),
+                         _p(np.ascontiguousarray(wh, np.float64), f64p),
+                         _p(np.ascontiguousarray(wv, np.float64), f64p), iters, ctypes.byref(cp),
+                         _p(u, f64p), _p(ph, f64p), _p(pv, f64p), _p(qh, f64p), _p(qv, f64p),
+                         init, _p(energy, f64p)), "refine")
+    return u, (ph, pv, qh, qv), energy
+
+
+def convex_gap(cost, wh, wv, u0, u, ph, pv, P: Params, alpha=None):
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    H, W, L = cost.shape
+    al = None if alpha is None else np.ascontiguousarray(np.broadcast_to(alpha, (H, W)), np.float64)
+    pr, du = ctypes.c_double(), ctypes.c_double()
+    cp = P.cont()
+    lib().or_convex_gap(H, W, L, _p(cost, f64p), None if al is None else _p(al, f64p),
+                        _p(np.ascontiguousarray(wh, np.float64), f64p),
+                        _p(np.ascontiguousarray(wv, np.float64), f64p), ctypes.byref(cp),
+                        _p(np.ascontiguousarray(u0, np.float64), f64p),
+                        _p(np.ascontiguousarray(u, np.float64), f64p),
+                        _p(np.ascontiguousarray(ph, np.float64), f64p),
+                        _p(np.ascontiguousarray(pv, np.float64), f64p),
+                        ctypes.byref(pr), ctypes.byref(du))
+    return pr.value, du.value
+
+
+def solve(left, right, L: int, dmm_iters: int, pd_iters: int, P: Params = Params(),
+          nthreads: int = 0):
+    """Whole path on the CPU: cost volume, Dual MM, refinement."""
+    cost = cost_volume(left, right, L, P.census_win)
+    wh, wv = edge_weights(left, P)
+    labels, lb, lam_h, lam_v = dmm(cost, wh, wv, dmm_iters, P, nthreads=nthreads)
+    u, st, en = refine(cost.astype(np.float64), wh.astype(np.float64), wv.astype(np.float64),
+                       labels.astype(np.float64), pd_iters, P)
+    return dict(cost=cost, wh=wh, wv=wv, labels=labels, lb=lb, lam_h=lam_h, lam_v=lam_v, u=u,
+                state=st, energy=en)

@@ -1,0 +1,188 @@
+"""Pins of the oracle's continuous stage (Sec. 2.4, 3.1) against the mathematics.
+
+Proximal maps and conjugates are checked against numeric minimisation and
+numeric suprema of their definitions; the whole primal-dual iteration is
+checked on the convex special case (C -> infinity) where the primal-dual gap
+must close, and on zero pairwise weights where it must reach the per-pixel
+minimiser; the continuous energy at integer labels must equal the discrete
+energy (Sec. 2.4: the same energy in both stages).
+"""
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1601_06274_gb300 import synthetic as S
+
+
+def _grid_argmin(f, lo, hi, n=200001):
+    xs = np.linspace(lo, hi, n)
+    v = f(xs)
+    k = int(np.argmin(v))
+    return xs[k], (hi - lo) / (n - 1)
+
+
+def test_interpolation():
+    c = np.array([3.0, 7.0, 1.0, 1.0, 9.0])
+    for k in range(5):
+        assert O.interp(c, k) == c[k]
+    assert O.interp(c, 0.25) == pytest.approx(4.0)
+    assert O.interp(c, 1.5) == pytest.approx(4.0)
+    assert O.interp(c, -2.0) == 3.0 and O.interp(c, 7.5) == 9.0
+
+
+def test_linearisation_slopes_and_box():
+    c = np.array([5.0, 2.0, 4.0, 10.0, 11.0, 0.0])
+    # at u0 = 2: s1 = D(2) - D(1) = 2, s2 = D(3) - D(2) = 6
+    assert O.linearise_px(c, 1.0, 2.0, 1.0) == pytest.approx((2.0, 6.0, 1.0, 3.0))
+    # at u0 = 1: s1 = -3, s2 = 2
+    assert O.linearise_px(c, 2.0, 1.0, 1.0) == pytest.approx((-6.0, 4.0, 0.0, 2.0))
+    # at u0 = 4: s1 = 1, s2 = -11 < s1 -> both the mean -5
+    assert O.linearise_px(c, 1.0, 4.0, 1.0) == pytest.approx((-5.0, -5.0, 3.0, 5.0))
+    # at the label range ends the argument is clamped: D(-1) = D(0)
+    assert O.linearise_px(c, 1.0, 0.0, 1.0) == pytest.approx((-1.5, -1.5, 0.0, 1.0))
+    assert O.linearise_px(c, 1.0, 0.5, 1.0)[2:] == pytest.approx((0.0, 1.5))
+
+
+def test_data_prox_is_argmin():
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        u0 = rng.uniform(2, 8)
+        s1, s2 = sorted(rng.uniform(-6, 6, size=2))
+        lo, hi = u0 - rng.uniform(0, 1.5), u0 + rng.uniform(0, 1.5)
+        tau = rng.uniform(0.05, 1.0)
+        uh = u0 + rng.uniform(-4, 4)
+
+        def obj(u):
+            d = np.where(u <= u0, s1 * (u - u0), s2 * (u - u0))
+            return d + (u - uh) ** 2 / (2 * tau)
+        ref, dx = _grid_argmin(obj, lo, hi)
+        assert O.prox_data(uh, u0, s1, s2, lo, hi, tau) == pytest.approx(ref, abs=2 * dx)
+
+
+@pytest.mark.parametrize("a,b", [(0.25, 1.0), (0.0, 2.75), (0.5, 2.0)])
+def test_conjugate_is_numeric_sup(a, b):
+    omega = 6.0
+    ts = np.linspace(-200, 200, 400001)
+    rt = omega * np.where(np.abs(ts) <= b, a * np.abs(ts), np.abs(ts) - b * (1 - a))
+    for s in np.linspace(-omega, omega, 41):
+        assert O.conj(s, omega, a, b) == pytest.approx(np.max(s * ts - rt), abs=1e-6)
+    assert O.conj(omega * 1.01, omega, a, b) == np.inf
+
+
+@pytest.mark.parametrize("a,b", [(0.25, 1.0), (0.0, 2.75), (0.5, 2.0)])
+def test_conjugate_prox_is_argmin(a, b):
+    rng = np.random.default_rng(1)
+    omega = 5.0
+    for _ in range(100):
+        t = rng.uniform(-12, 12)
+        step = rng.uniform(0.05, 2.0)
+
+        def obj(s):
+            g = b * np.maximum(0.0, np.abs(s) - omega * a)
+            return step * g + (s - t) ** 2 / 2
+
+        ref, dx = _grid_argmin(obj, -omega, omega)
+        assert O.prox_conj(t, omega, a, b, step) == pytest.approx(ref, abs=2 * dx)
+
+
+def test_continuous_energy_at_labels_equals_discrete_energy():
+    sp = S.make_workload(S.SMALL, seed=1)
+    cost = O.cost_volume(sp.left, sp.right, 16)
+    wh, wv = O.edge_weights(sp.left)
+    rng = np.random.default_rng(2)
+    for _ in range(3):
+        labels = rng.integers(0, 16, size=cost.shape[:2]).astype(np.uint16)
+        e_d = O.discrete_energy(cost, wh, wv, labels)
+        e_c = O.cont_energy(cost.astype(float), wh.astype(float), wv.astype(float),
+                            labels.astype(float))
+        assert e_c == pytest.approx(e_d, abs=1e-9)
+
+
+def _small_problem(seed=3):
+    sp = S.make_pair(12, 16, 16, planes=3, seed=seed)
+    cost = O.cost_volume(sp.left, sp.right, 16).astype(float)
+    wh, wv = O.edge_weights(sp.left)
+    u0 = np.random.default_rng(seed).uniform(0, 15, size=(12, 16))
+    return cost, wh.astype(float), wv.astype(float), u0
+
+
+def test_convex_case_gap_closes():
+    # C -> infinity removes R- (q stays 0): min_u D~(u) + R+(Au) is convex and the
+    # primal-dual gap of Eq. (cont_nonlin_pd) must vanish
+    cost, wh, wv, u0 = _small_problem()
+    for lam_r in (1.0, 4.0):
+        P = O.Params(C=1e7, warps=1, lambda_r=lam_r)
+        u, (ph, pv, qh, qv), _ = O.refine(cost, wh, wv, u0, 20000, P)
+        assert np.all(qh == 0) and np.all(qv == 0)
+        pr, du = O.convex_gap(cost, wh, wv, u0, u, ph, pv, P)
+        assert abs(pr - du) <= 1e-9 * abs(pr)
+
+
+def test_zero_weights_reach_pixelwise_minimiser():
+    cost, wh, wv, u0 = _small_problem(4)
+    P = O.Params(warps=1)
+    u, _, _ = O.refine(cost, 0 * wh, 0 * wv, u0, 200, P)
+    for y in range(12):
+        for x in range(16):
+            s1, s2, lo, hi = O.linearise_px(cost[y, x], 1.0, u0[y, x], 1.0)
+            ref = u0[y, x] if s1 <= 0 <= s2 else (lo if s1 > 0 else hi)
+            assert u[y, x] == pytest.approx(ref, abs=1e-12)
+
+
+def test_dual_feasibility_and_box():
+    sp = S.make_workload(S.SMALL, seed=2)
+    cost = O.cost_volume(sp.left, sp.right, 16)
+    wh, wv = O.edge_weights(sp.left)
+    labels, _, _, _ = O.dmm(cost, wh, wv, 3)
+    P = O.Params(lambda_r=1.5)
+    u, (ph, pv, qh, qv), en = O.refine(cost.astype(float), wh.astype(float), wv.astype(float),
+                                       labels.astype(float), 50, P)
+    for arr, w in ((ph, wh), (pv, wv), (qh, wh), (qv, wv)):
+        assert np.all(np.abs(arr) <= 1.5 * w + 1e-12)
+    assert np.all(u >= 0) and np.all(u <= 15)
+    # 5 warps of half-width 1 around the labels
+    assert np.all(np.abs(u - labels) <= 5.0 + 1e-12)
+
+
+# --- planted mistakes: each must be caught by the convex-gap pin -------------
+
+MUTATIONS = [
+    ("sign of A^T in the primal step", "u[p] - tau * div", "u[p] + tau * div"),
+    ("no extrapolation in the dual step",
+     "double ext = (2.0 * un[p] - u[p]) - (2.0 * un[p + 1] - u[p + 1]);",
+     "double ext = un[p] - un[p + 1];"),
+    ("data prox middle case returns the input", "else v = u0;", "else v = uh;"),
+    ("dual prox without the clamp", "if (tp > omega) tp = omega;", "(void)0;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS)
+def test_pins_catch_planted_mistakes(tmp_path, name, old, new):
+    src = open(os.path.join(os.path.dirname(O.__file__), "dm_oracle.c")).read()
+    assert old in src, name
+    mut = tmp_path / "mut.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(mut), "-lm"],
+                   check=True)
+    lib = ctypes.CDLL(str(so))
+    f64p = ctypes.POINTER(ctypes.c_double)
+    lib.or_refine.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4 + [ctypes.c_int,
+                              ctypes.POINTER(O.ContParams)] + [f64p] * 5 + [ctypes.c_int, f64p])
+    cost, wh, wv, u0 = _small_problem()
+    H, W, L = cost.shape
+    P = O.Params(C=1e7, warps=1, lambda_r=4.0)
+    u = u0.copy()
+    st = [np.zeros((H, W)) for _ in range(4)]
+    en = np.zeros(1)
+    cp = P.cont()
+    p = lambda a: a.ctypes.data_as(f64p)
+    lib.or_refine(H, W, L, p(cost), None, p(wh), p(wv), 20000, ctypes.byref(cp), p(u),
+                  *[p(s) for s in st], 1, p(en))
+    pr, du = O.convex_gap(cost, wh, wv, u0, u, st[0], st[1], P)
+    assert not (np.isfinite(pr) and abs(pr - du) <= 1e-9 * abs(pr)), f"not caught: {name}"
