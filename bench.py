@@ -1,0 +1,290 @@
+#!/usr/bin/env python
+"""Throughput of the stereo hot path (census cost volume -> Dual MM ->
+primal-dual refinement) on one synthetic KITTI-shaped frame per step.
+
+One step = one frame of 1242x375 pixels with 128 labels: cost volume, 10 Dual
+MM iterations (horizontal + vertical pass each), 100 primal-dual iterations
+in 5 warps.  Inputs are resident on the GPU when the timed region starts; L2
+is flushed (a 256 MB write) between steps, outside the timed events.
+
+Prints one JSON line (rank 0).  With --impl reference the CPU oracle is timed
+instead, on a bounded crop of the same workload.  Under torchrun each rank
+solves its own frame (replicas; weak scaling; no collective on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel·labels/s (discrete+continuous) at 1242×375×128"
+UNIT = "Mpixel·labels/s"
+CPU_SAMPLE_ROWS = 24
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded crop (the cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def cpu_sample(rows: int = CPU_SAMPLE_ROWS):
+    from paper_1601_06274_gb300 import synthetic as S
+    spec = S.KITTI
+    sp = S.make_workload(spec, seed=0)
+    return sp.left[:rows].copy(), sp.right[:rows].copy(), spec
+
+
+def time_oracle(left, right, spec):
+    from oracle import oracle as O
+    O.lib()
+    t0 = time.perf_counter()
+    O.solve(left, right, spec["L"], spec["dmm_iters"], spec["pd_iters"], nthreads=os.cpu_count())
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    left, right, spec = cpu_sample()
+    units = left.shape[0] * left.shape[1] * spec["L"]
+    for _ in range(args.warmup):
+        time_oracle(left, right, spec)
+    ts = [time_oracle(left, right, spec) for _ in range(args.steps)]
+    tot = sum(ts)
+    value = units * args.steps / tot / 1e6
+    sample = (f"rows 0-{left.shape[0] - 1} of the 1242x375x128 frame (a {left.shape[1]}x"
+              f"{left.shape[0]}x{spec['L']} crop), {spec['dmm_iters']} Dual MM + "
+              f"{spec['pd_iters']} PD iterations per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * tot / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
+        "config": {"workload": "kitti-1242x375x128 (cpu crop)", "dmm_iters": spec["dmm_iters"],
+                   "pd_iters": spec["pd_iters"]},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        import torch
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+        try:
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(device_index).uuid)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", uuid, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as distd
+        torch.cuda.set_device(local)
+        distd.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_1601_06274_gb300 import build, dm, synthetic as S
+    build.build()
+    spec = S.KITTI
+    H, W, L = spec["H"], spec["W"], spec["L"]
+    NI, NP = spec["dmm_iters"], spec["pd_iters"]
+    sp = S.make_workload(spec, seed=rank)
+    ctx = dm.Context(H, W, L, device=str(dev))
+    stream = ctx.stream
+    d_left = torch.from_numpy(sp.left).to(dev)
+    d_right = torch.from_numpy(sp.right).to(dev)
+    d_u = torch.empty((H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        ctx.solve(d_left, d_right, NI, NP, out=d_u)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K frames, events per frame, L2 flushed between frames
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    launches0 = ctx.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(dev.index or 0)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            evs[k][0].record(stream)
+            ctx.solve(d_left, d_right, NI, NP, out=d_u)
+            evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    launches = ctx.launch_count() - launches0
+    ctx.sync()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(ms)
+    t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    tot_ms = float(t.item())
+    units = H * W * L
+    value = units * args.steps * ws / (tot_ms / 1e3) / 1e6
+
+    # ---- end to end through the C ABI with pinned host buffers
+    h_left = torch.from_numpy(sp.left).pin_memory()
+    h_right = torch.from_numpy(sp.right).pin_memory()
+    h_u = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    ctx.solve_host(h_left, h_right, NI, NP, h_u)
+    e_ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.solve_host(h_left, h_right, NI, NP, h_u)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e_ms.append(a.elapsed_time(b))
+    e2e_value = units * args.steps * ws / (sum(e_ms) / 1e3) / 1e6
+
+    # ---- dominant kernel: one Dual MM pass per launch, CUDA events on the ctx stream
+    ctx.cost_volume(d_left, d_right)
+    pass_ms = {0: [], 1: []}
+    for _ in range(max(1, args.steps // 2)):
+        ctx.reset_duals()
+        for it in range(NI):
+            for which in (0, 1):
+                flush.fill_(it & 0xff)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.discrete_pass(which)
+                b.record(stream)
+                pass_ms[which].append((a, b))
+    torch.cuda.synchronize()
+    avg = {w: sum(a.elapsed_time(b) for a, b in v) / len(v) for w, v in pass_ms.items()}
+    # algorithmic bytes per launch (int32 duals): horizontal pass reads c (1 B) and
+    # lambda_v (4 B) and writes lambda_h (4 B) per pixel-label; vertical pass reads
+    # lambda_h and writes lambda_v (8 B)
+    bytes_per = {0: 9 * units, 1: 8 * units}
+    dom = max((0, 1), key=lambda w: avg[w])
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback"
+    if os.path.exists(peaks_path):
+        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+    achieved = bytes_per[dom] / (avg[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "dmm_pass_kernel (" + ("horizontal" if dom == 0 else "vertical") + ")",
+                "peak_source": peak_src,
+                "pass_ms": {"horizontal": round(avg[0], 4), "vertical": round(avg[1], 4)}}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        left_c, right_c, _ = cpu_sample()
+        t_cpu = time_oracle(left_c, right_c, spec)
+        cpu = {"value": round(left_c.shape[0] * W * L / t_cpu / 1e6, 4), "unit": UNIT,
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"rows 0-{CPU_SAMPLE_ROWS - 1} ({W}x{CPU_SAMPLE_ROWS}x{L} crop) of the "
+                         f"frame, {NI} Dual MM + {NP} PD iterations, {t_cpu:.2f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(tot_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
+            "config": {"workload": "kitti-1242x375x128", "H": H, "W": W, "L": L,
+                       "dmm_iters": NI, "pd_iters": NP, "warps": 5,
+                       "l2": "flushed between steps (256 MB write, outside the timed events)",
+                       "parallelism": f"replicas{ws}"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 2 * H * W,
+                    "d2h_bytes_per_step": 4 * H * W},
+            "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

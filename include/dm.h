@@ -1,0 +1,183 @@
+/*
+ * dm.h -- C ABI of the GB300 dense-matching library (libdm.so).
+ *
+ * The library computes the data-parallel hot path of the discrete-continuous
+ * stereo method of arXiv 1601.06274 ("Solving Dense Image Matching in
+ * Real-Time using Discrete-Continuous Optimization"):
+ *
+ *   1. census transform and matching-cost volume  (Sec. 3.1; Sec. 1)
+ *   2. Dual MM over horizontal and vertical chains (Sec. 2.3, Alg. Dual_MM)
+ *      with hierarchical minorants               (App. A, Alg. Handshake)
+ *   3. non-linear primal-dual refinement           (Sec. 2.4, Eq. cont_iterates;
+ *                                                   Sec. 3.1 data term and prox)
+ *
+ * Conventions shared by every entry point
+ *   - Images are H x W, row-major, uint8, one byte per pixel (no padding).
+ *   - The cost volume is [H][W][L] uint8, labels innermost; label l is the
+ *     disparity l pixels (right-image pixel x - l).
+ *   - Edge weights omega are [H][W] uint8: wh[y][x] belongs to the edge
+ *     (y,x)-(y,x+1), wv[y][x] to (y,x)-(y+1,x); entries without an edge are
+ *     ignored.
+ *   - Dual variables lambda_h, lambda_v are [H][W][L] int32.
+ *   - "d_" pointers are device pointers, "h_" pointers host pointers.  All
+ *     device memory is owned by the caller.  The context owns host memory
+ *     only; its device workspace is caller-allocated and bound with
+ *     dm_bind_workspace().
+ *   - Every call is asynchronous on the context's stream (default stream 0)
+ *     unless stated otherwise; device outputs are valid once the stream has
+ *     been synchronised.  Calls that return host data synchronise the stream.
+ *   - Every entry point returns a status code (DM_OK on success).  No
+ *     exception crosses the ABI.  Device-side faults detected by the kernels
+ *     (e.g. an edge weight with no integer penalty table) are recorded in the
+ *     workspace and reported as DM_ERR_DEVICE by the next synchronising call.
+ *   - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef DM_H
+#define DM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DM_API __attribute__((visibility("default")))
+#else
+#define DM_API
+#endif
+
+/* status codes */
+#define DM_OK            0
+#define DM_ERR_ARG       1  /* invalid argument (null pointer, size, parameter)   */
+#define DM_ERR_CUDA      2  /* a CUDA runtime call failed                          */
+#define DM_ERR_RANGE     3  /* a value does not fit the storage type               */
+#define DM_ERR_TIMEOUT   4  /* a bounded device-side wait gave up                  */
+#define DM_ERR_STATE     5  /* call order (e.g. no workspace, no cost volume yet)  */
+#define DM_ERR_WORKSPACE 6  /* bound workspace too small or misaligned             */
+#define DM_ERR_DEVICE    7  /* a kernel flagged invalid data                       */
+
+/*
+ * Parameters.  Defaults (dm_default_params) are the readings of the paper
+ * used throughout: 5x5 census; omega = 8 if |I1(i) - I1(j)| < 16 else 4;
+ * r of Eq. (r-decompose) with eps = 1/4, delta = 1, C = 2; tau = sigma =
+ * 0.35; h = 1 label; 5 warps (Sec. 4.1.2 uses 5 warps).
+ *
+ * Discrete stage: the pairwise term of the edge ij is omega_ij * r(|x_i - x_j|)
+ * with r sampled at integer label distances; every omega in 0..255 for which
+ * omega*r(t) is an integer for all t is usable, and the table must reach its
+ * cap omega*C within 4 label steps.
+ * Continuous stage: the regulariser is lambda_r * omega_ij * r((Au)_ij).
+ */
+typedef struct dm_params {
+    uint32_t struct_size;   /* sizeof(dm_params); checked by dm_create          */
+    int32_t census_win;     /* 3 or 5                                            */
+    int32_t edge_threshold; /* T of the edge-weight rule                         */
+    int32_t w_hi, w_lo;     /* omega for |I(i) - I(j)| < T and otherwise         */
+    double eps, delta, C;   /* penalty r (Eq. r-decompose)                       */
+    double lambda_r;        /* regularisation weight of the continuous stage     */
+    double alpha;           /* data-term weight of the continuous stage          */
+    double tau, sigma;      /* primal and dual step sizes (Eq. cont_iterates)    */
+    double h;               /* linearisation half-width in labels (Sec. 3.1)    */
+    int32_t warps;          /* re-linearisations of the data term (Sec. 3.1)    */
+    int32_t reserved[7];
+} dm_params;
+
+typedef struct dm_ctx dm_ctx;
+
+/* Fill *p with the defaults.  DM_ERR_ARG if p is NULL. */
+DM_API int dm_default_params(dm_params* p);
+
+/* Create a context for H x W images and L labels (2 <= L <= 256,
+ * 1 <= H, W <= 65535, H*W*L < 2^31).  Copies *p.  On success *out owns host
+ * memory only; release it with dm_destroy.  DM_ERR_ARG for invalid sizes or
+ * parameters.  If omega*r is not an integer table reaching its cap within 4
+ * labels for w_hi or w_lo, the context is still created (the continuous
+ * stage works) but dm_discrete and dm_discrete_pass return DM_ERR_ARG. */
+DM_API int dm_create(int H, int W, int L, const dm_params* p, dm_ctx** out);
+
+/* Release a context (NULL is a no-op).  Does not free the workspace. */
+DM_API int dm_destroy(dm_ctx* ctx);
+
+/* Bytes of device workspace the context needs (256-byte aligned start). */
+DM_API int dm_workspace_bytes(const dm_ctx* ctx, size_t* bytes);
+
+/* Bind caller-owned device memory of at least dm_workspace_bytes() bytes,
+ * 256-byte aligned (DM_ERR_WORKSPACE otherwise).  Resets all state. */
+DM_API int dm_bind_workspace(dm_ctx* ctx, void* d_workspace, size_t bytes);
+
+/* Stream for all later work (a cudaStream_t passed as void*; NULL = 0). */
+DM_API int dm_set_stream(dm_ctx* ctx, void* stream);
+
+/* Census transform of both images and the cost volume (Sec. 3.1):
+ * c[y][x][l] = popcount(census_L(y,x) ^ census_R(y,x-l)), or win*win-1 when
+ * x-l < 0; census bits are [I(neighbour) < I(centre)] over the window with
+ * clamp-to-edge borders.  Also computes the edge weights from d_left.
+ * Resets the dual variables. */
+DM_API int dm_cost_volume(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right);
+
+/* Use a caller-made cost volume and edge weights (copied into the
+ * workspace).  Resets the dual variables. */
+DM_API int dm_set_cost_volume(dm_ctx* ctx, const uint8_t* d_cost, const uint8_t* d_wh,
+                              const uint8_t* d_wv);
+
+/* Zero both dual variables (a cold start of Alg. Dual_MM). */
+DM_API int dm_reset_duals(dm_ctx* ctx);
+
+/* One half-iteration of Alg. Dual_MM (which = 0: horizontal chains with
+ * unaries c + lambda_v, writes lambda_h; which = 1: vertical chains with
+ * unaries lambda_h, writes lambda_v).  For tests and instrumentation. */
+DM_API int dm_discrete_pass(dm_ctx* ctx, int which);
+
+/* iters full iterations of Alg. Dual_MM (horizontal then vertical pass)
+ * from the current duals, then the labelling x_i = argmin_l
+ * (lambda_h + lambda_v)_i(l) (ties: smallest l) and the lower bound
+ * sum_i min_l (lambda_h + lambda_v)_i(l) of every iteration.  h_lb
+ * (nullable) receives the iters bounds and makes the call synchronous. */
+DM_API int dm_discrete(dm_ctx* ctx, int iters, int64_t* h_lb);
+
+/* Primal-dual refinement (Sec. 2.4 and 3.1): iters iterations split evenly
+ * over params.warps re-linearisations, starting from d_u0 (H x W float32,
+ * device; NULL = the labels of the last dm_discrete).  p and q start at 0. */
+DM_API int dm_refine(dm_ctx* ctx, int iters, const float* d_u0);
+
+/* The whole path: cost volume, dmm_iters iterations of Dual MM, pd_iters
+ * primal-dual iterations; the refined disparity (H x W float32) is written
+ * to d_u (device). */
+DM_API int dm_solve(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int dmm_iters,
+                    int pd_iters, float* d_u);
+
+/* Same with host buffers: copies the images in and the disparity (and, if
+ * h_labels is not NULL, the labels) out through the workspace; synchronous. */
+DM_API int dm_solve_host(dm_ctx* ctx, const uint8_t* h_left, const uint8_t* h_right,
+                         int dmm_iters, int pd_iters, float* h_u, uint16_t* h_labels);
+
+/* Copies of internal state into caller device buffers. */
+DM_API int dm_get_labels(dm_ctx* ctx, uint16_t* d_labels);            /* H*W        */
+DM_API int dm_get_disparity(dm_ctx* ctx, float* d_u);                 /* H*W        */
+DM_API int dm_get_duals(dm_ctx* ctx, int32_t* d_lam_h, int32_t* d_lam_v); /* H*W*L each */
+DM_API int dm_get_cost_volume(dm_ctx* ctx, uint8_t* d_cost, uint8_t* d_wh, uint8_t* d_wv);
+
+/* Lower bounds of the last dm_discrete call (n <= iters of that call);
+ * synchronous. */
+DM_API int dm_get_lower_bounds(dm_ctx* ctx, int64_t* h_lb, int n);
+
+/* Continuous energy E(u) = sum alpha D_i(u_i) + sum lambda_r omega r((Au)_e)
+ * (Eq. mrf_formulation) of the current disparity; synchronous. */
+DM_API int dm_energy(dm_ctx* ctx, double* h_energy);
+
+/* Number of kernels this context has enqueued since dm_create (host-side
+ * counter; instrumentation for benchmarks). */
+DM_API int dm_launch_count(const dm_ctx* ctx, uint64_t* count);
+
+/* Synchronise the stream and report a device-side error, if any. */
+DM_API int dm_sync(dm_ctx* ctx);
+
+/* Static description of a status code. */
+DM_API const char* dm_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DM_H */

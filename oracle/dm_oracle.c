@@ -265,40 +265,29 @@ void or_hier_minorant(int n, int K, const i64* theta, const i64* V, i64* lam)
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-    int ntab;          /* distinct omegas */
-    int omega[8];
-    i64* table[8];     /* K entries each */
+    i64* table[256];   /* omega -> K entries (built on first use) */
 } or_tables;
 
 static int build_tables(or_tables* T, int K, const int32_t* w, int count, double eps,
                         double delta, double C)
 {
-    T->ntab = 0;
+    for (int t = 0; t < 256; ++t) T->table[t] = NULL;
     for (int e = 0; e < count; ++e) {
         int om = w[e];
-        int found = 0;
-        for (int t = 0; t < T->ntab; ++t) if (T->omega[t] == om) found = 1;
-        if (found) continue;
-        if (T->ntab == 8) return OR_ERR_ARG;
-        T->omega[T->ntab] = om;
-        T->table[T->ntab] = (i64*)malloc((size_t)K * sizeof(i64));
-        int rc = or_penalty_table(om, eps, delta, C, K, T->table[T->ntab]);
+        if (om < 0 || om > 255) return OR_ERR_ARG;
+        if (T->table[om]) continue;
+        T->table[om] = (i64*)malloc((size_t)K * sizeof(i64));
+        int rc = or_penalty_table(om, eps, delta, C, K, T->table[om]);
         if (rc) return rc;
-        T->ntab++;
     }
     return OR_OK;
 }
 
-static const i64* find_table(const or_tables* T, int om)
-{
-    for (int t = 0; t < T->ntab; ++t) if (T->omega[t] == om) return T->table[t];
-    return NULL;
-}
+static const i64* find_table(const or_tables* T, int om) { return T->table[om]; }
 
 static void free_tables(or_tables* T)
 {
-    for (int t = 0; t < T->ntab; ++t) free(T->table[t]);
-    T->ntab = 0;
+    for (int t = 0; t < 256; ++t) free(T->table[t]);
 }
 
 /* One pass of Alg. Dual_MM.

@@ -270,9 +270,9 @@ def cont_energy(cost, wh, wv, u, P: Params = Params(), alpha=None) -> float:
     cost = np.ascontiguousarray(cost, dtype=np.float64)
     H, W, L = cost.shape
     u = np.ascontiguousarray(u, dtype=np.float64)
-    al = None if alpha is None else np.ascontiguousarray(np.broadcast_to(alpha, (H, W)), np.float64)
+    al = np.ascontiguousarray(np.broadcast_to(P.alpha if alpha is None else alpha, (H, W)), np.float64)
     cp = P.cont()
-    return lib().or_cont_energy(H, W, L, _p(cost, f64p), None if al is None else _p(al, f64p),
+    return lib().or_cont_energy(H, W, L, _p(cost, f64p), _p(al, f64p),
                                 _p(np.ascontiguousarray(wh, np.float64), f64p),
                                 _p(np.ascontiguousarray(wv, np.float64), f64p),
                                 ctypes.byref(cp), _p(u, f64p))
@@ -289,10 +289,10 @@ def refine(cost, wh, wv, u0, iters: int, P: Params = Params(), alpha=None, state
     else:
         ph, pv, qh, qv = (np.array(s, dtype=np.float64).copy() for s in state)
         init = 0
-    al = None if alpha is None else np.ascontiguousarray(np.broadcast_to(alpha, (H, W)), np.float64)
+    al = np.ascontiguousarray(np.broadcast_to(P.alpha if alpha is None else alpha, (H, W)), np.float64)
     energy = np.zeros(P.warps)
     cp = P.cont()
-    _chk(lib().or_refine(H, W, L, _p(cost, f64p), None if al is None else _p(al, f64p),
+    _chk(lib().or_refine(H, W, L, _p(cost, f64p), _p(al, f64p),
                          _p(np.ascontiguousarray(wh, np.float64), f64p),
                          _p(np.ascontiguousarray(wv, np.float64), f64p), iters, ctypes.byref(cp),
                          _p(u, f64p), _p(ph, f64p), _p(pv, f64p), _p(qh, f64p), _p(qv, f64p),
@@ -303,10 +303,10 @@ def refine(cost, wh, wv, u0, iters: int, P: Params = Params(), alpha=None, state
 def convex_gap(cost, wh, wv, u0, u, ph, pv, P: Params, alpha=None):
     cost = np.ascontiguousarray(cost, dtype=np.float64)
     H, W, L = cost.shape
-    al = None if alpha is None else np.ascontiguousarray(np.broadcast_to(alpha, (H, W)), np.float64)
+    al = np.ascontiguousarray(np.broadcast_to(P.alpha if alpha is None else alpha, (H, W)), np.float64)
     pr, du = ctypes.c_double(), ctypes.c_double()
     cp = P.cont()
-    lib().or_convex_gap(H, W, L, _p(cost, f64p), None if al is None else _p(al, f64p),
+    lib().or_convex_gap(H, W, L, _p(cost, f64p), _p(al, f64p),
                         _p(np.ascontiguousarray(wh, np.float64), f64p),
                         _p(np.ascontiguousarray(wv, np.float64), f64p), ctypes.byref(cp),
                         _p(np.ascontiguousarray(u0, np.float64), f64p),

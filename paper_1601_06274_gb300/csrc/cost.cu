@@ -1,0 +1,116 @@
+// Census transform, edge weights and matching-cost volume (Sec. 3.1 of
+// arXiv 1601.06274: census on a small patch, pixel-wise Hamming distance;
+// Sec. 1: the cost is precomputed for every label).
+//
+// census: one thread per pixel, both images in one launch (blockIdx.z picks
+//   the image); the 5x5 (or 3x3) window is read through L1 with
+//   clamp-to-edge indices.  Bit k is the k-th neighbour in raster order,
+//   centre skipped, set when I(neighbour) < I(centre).  The left image's
+//   threads also write the edge weights omega (Sec. 2.1: image dependent,
+//   weaker across intensity edges).
+// cost:   c[y][x][l] = popcount(cL[y][x] ^ cR[y][x-l]) or win*win-1 when
+//   x - l < 0.  One thread writes 16 consecutive labels of one pixel as a
+//   single 16-byte store, so a warp writes 512 contiguous bytes.
+
+#include "dm_internal.cuh"
+
+namespace dm {
+namespace {
+
+template <int WIN>
+__global__ void census_edges_kernel(const uint8_t* __restrict__ left,
+                                    const uint8_t* __restrict__ right, int H, int W, int T,
+                                    int w_hi, int w_lo, uint32_t* __restrict__ census,
+                                    uint8_t* __restrict__ wh, uint8_t* __restrict__ wv)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int img = blockIdx.z;
+    if (x >= W || y >= H) return;
+    const uint8_t* I = img == 0 ? left : right;
+    constexpr int r = WIN / 2;
+    const int centre = I[y * W + x];
+    uint32_t code = 0;
+    int bit = 0;
+#pragma unroll
+    for (int dy = -r; dy <= r; ++dy) {
+        const int yy = min(max(y + dy, 0), H - 1);
+#pragma unroll
+        for (int dx = -r; dx <= r; ++dx) {
+            if (dy == 0 && dx == 0) continue;
+            const int xx = min(max(x + dx, 0), W - 1);
+            code |= (uint32_t)(I[yy * W + xx] < centre) << bit;
+            ++bit;
+        }
+    }
+    census[(size_t)img * H * W + (size_t)y * W + x] = code;
+    if (img == 0) {
+        const size_t i = (size_t)y * W + x;
+        uint8_t a = 0, b = 0;
+        if (x + 1 < W) a = (uint8_t)(abs(centre - (int)I[i + 1]) < T ? w_hi : w_lo);
+        if (y + 1 < H) b = (uint8_t)(abs(centre - (int)I[i + W]) < T ? w_hi : w_lo);
+        wh[i] = a;
+        wv[i] = b;
+    }
+}
+
+__global__ void cost_kernel(const uint32_t* __restrict__ cl, const uint32_t* __restrict__ cr,
+                            int H, int W, int L, int maxc, uint8_t* __restrict__ cost)
+{
+    // one thread: pixel p, labels [16 g, 16 g + 16)
+    const int groups = (L + 15) >> 4;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)H * W * groups;
+    if (t >= total) return;
+    const int g = (int)(t % groups);
+    const long long p = t / groups;
+    const int x = (int)(p % W);
+    const uint32_t a = cl[p];
+    const int l0 = g << 4;
+    uint8_t v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int l = l0 + k;
+        const int xr = x - l;
+        v[k] = (uint8_t)(xr >= 0 ? __popc(a ^ cr[p - l]) : maxc);
+    }
+    uint8_t* dst = cost + p * L + l0;
+    if ((L & 15) == 0) {
+        uint4 w;
+        w.x = v[0] | (v[1] << 8) | (v[2] << 16) | ((uint32_t)v[3] << 24);
+        w.y = v[4] | (v[5] << 8) | (v[6] << 16) | ((uint32_t)v[7] << 24);
+        w.z = v[8] | (v[9] << 8) | (v[10] << 16) | ((uint32_t)v[11] << 24);
+        w.w = v[12] | (v[13] << 8) | (v[14] << 16) | ((uint32_t)v[15] << 24);
+        *reinterpret_cast<uint4*>(dst) = w;
+    } else {
+        for (int k = 0; k < 16 && l0 + k < L; ++k) dst[k] = v[k];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_census_edges(const uint8_t* left, const uint8_t* right, int H, int W, int win,
+                                int T, int w_hi, int w_lo, uint32_t* census, uint8_t* wh,
+                                uint8_t* wv, cudaStream_t s)
+{
+    dim3 blk(32, 8);
+    dim3 grd((W + 31) / 32, (H + 7) / 8, 2);
+    if (win == 5)
+        census_edges_kernel<5><<<grd, blk, 0, s>>>(left, right, H, W, T, w_hi, w_lo, census, wh, wv);
+    else
+        census_edges_kernel<3><<<grd, blk, 0, s>>>(left, right, H, W, T, w_hi, w_lo, census, wh, wv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cost(const uint32_t* census, int H, int W, int L, int maxc, uint8_t* cost,
+                        cudaStream_t s)
+{
+    const long long total = (long long)H * W * ((L + 15) / 16);
+    const int threads = 256;
+    const long long blocks = (total + threads - 1) / threads;
+    cost_kernel<<<(unsigned)blocks, threads, 0, s>>>(census, census + (size_t)H * W, H, W, L, maxc,
+                                                     cost);
+    return cudaGetLastError();
+}
+
+}  // namespace dm

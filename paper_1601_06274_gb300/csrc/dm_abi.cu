@@ -1,0 +1,558 @@
+// C ABI of libdm.so (declared in include/dm.h): context, workspace layout,
+// argument checking and the launch sequence of the stereo hot path of
+// arXiv 1601.06274 (cost volume -> Dual MM -> primal-dual refinement).
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dm_internal.cuh"
+
+struct dm_ctx {
+    int H = 0, W = 0, L = 0, KP = 0, lpt = 0, radius = 1;
+    bool discrete_ok = true;    // w_hi and w_lo have integer penalty taps within kRMax
+    dm_params p{};
+    dm::Layout lay{};
+    uint8_t* ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<int32_t> taps;  // [256][kTapW]
+    bool have_cost = false;
+    bool have_labels = false;
+    bool have_u = false;
+    int u_cur = 0;              // 0: current disparity in lay.u, 1: in lay.u_new
+    int last_iters = 0;
+    unsigned long long launches = 0;  // kernels enqueued by this context
+};
+
+namespace {
+
+constexpr int kMaxIters = 4096;
+
+#define DM_CK(call)                                  \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return DM_ERR_CUDA;   \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+double r_ab(double t, double a, double b)
+{
+    const double at = std::fabs(t);
+    return at <= b ? a * at : at - b * (1.0 - a);
+}
+
+// r = r_{eps,delta} - r_{0, C + delta - eps delta}  (Eq. r-decompose)
+double r_dc(double t, const dm_params& p)
+{
+    return r_ab(t, p.eps, p.delta) - r_ab(t, 0.0, p.C + p.delta - p.eps * p.delta);
+}
+
+bool is_int(double v, long long* out)
+{
+    const double rv = std::nearbyint(v);
+    if (std::fabs(v - rv) > 1e-9) return false;
+    *out = (long long)rv;
+    return true;
+}
+
+// Taps of omega * r sampled at label distances (Sec. 2.2, Fig. 2).  Returns the
+// number of distances below the cap (the window radius), or -1 if omega * r is
+// not an integer table that reaches its cap within kRMax steps.
+int build_taps(int omega, int L, const dm_params& p, int32_t* row)
+{
+    std::memset(row, 0, sizeof(int32_t) * dm::kTapW);
+    long long cap;
+    if (!is_int(omega * p.C, &cap)) return -1;
+    int radius = 0;
+    long long prev = 0;
+    for (int t = 1; t < (L > dm::kRMax + 2 ? L : dm::kRMax + 2); ++t) {
+        long long v;
+        if (!is_int(omega * r_dc((double)t, p), &v)) return -1;
+        if (v < prev || v > cap) return -1;
+        if (v < cap) {
+            if (t > dm::kRMax) return -1;
+            radius = t;
+        } else if (t <= dm::kRMax) {
+            // at or beyond the cap: later taps are redundant, keep them at the cap
+        }
+        if (t <= dm::kRMax) row[t - 1] = (int32_t)(v < cap ? v : cap);
+        prev = v;
+    }
+    row[dm::kTapP2] = (int32_t)cap;
+    row[dm::kTapValid] = 1;
+    return radius;
+}
+
+bool params_ok(const dm_params& p)
+{
+    if (p.struct_size != sizeof(dm_params)) return false;
+    if (p.census_win != 3 && p.census_win != 5) return false;
+    if (p.w_hi < 0 || p.w_hi > 255 || p.w_lo < 0 || p.w_lo > 255) return false;
+    if (!(p.eps >= 0.0 && p.eps <= 1.0 && p.delta > 0.0 && p.C >= p.eps * p.delta)) return false;
+    if (!(p.lambda_r >= 0.0 && p.alpha >= 0.0 && p.tau > 0.0 && p.sigma > 0.0 && p.h > 0.0))
+        return false;
+    if (p.warps < 1) return false;
+    return true;
+}
+
+dm::PdArgs pd_args(dm_ctx* c)
+{
+    dm::PdArgs a{};
+    uint8_t* ws = c->ws;
+    const dm::Layout& l = c->lay;
+    a.H = c->H;
+    a.W = c->W;
+    a.L = c->L;
+    a.cost = ws + l.cost;
+    a.wh = ws + l.wh;
+    a.wv = ws + l.wv;
+    a.alpha = (float)c->p.alpha;
+    a.lambda_r = (float)c->p.lambda_r;
+    a.tau = (float)c->p.tau;
+    a.sigma = (float)c->p.sigma;
+    a.h = (float)c->p.h;
+    a.ap = (float)c->p.eps;
+    a.bp = (float)c->p.delta;
+    a.bq = (float)(c->p.C + c->p.delta - c->p.eps * c->p.delta);
+    float* ua = reinterpret_cast<float*>(ws + l.u);
+    float* ub = reinterpret_cast<float*>(ws + l.u_new);
+    a.u = c->u_cur == 0 ? ua : ub;
+    a.u_new = c->u_cur == 0 ? ub : ua;
+    a.u0 = reinterpret_cast<float*>(ws + l.u0);
+    a.s1 = reinterpret_cast<float*>(ws + l.s1);
+    a.s2 = reinterpret_cast<float*>(ws + l.s2);
+    a.lo = reinterpret_cast<float*>(ws + l.lo);
+    a.hi = reinterpret_cast<float*>(ws + l.hi);
+    a.ph = reinterpret_cast<float*>(ws + l.ph);
+    a.pv = reinterpret_cast<float*>(ws + l.pv);
+    a.qh = reinterpret_cast<float*>(ws + l.qh);
+    a.qv = reinterpret_cast<float*>(ws + l.qv);
+    return a;
+}
+
+int check_device_error(dm_ctx* c)
+{
+    int32_t err = 0;
+    DM_CK(cudaMemcpyAsync(&err, c->ws + c->lay.err, sizeof(err), cudaMemcpyDeviceToHost,
+                          c->stream));
+    DM_CK(cudaStreamSynchronize(c->stream));
+    return err != 0 ? DM_ERR_DEVICE : DM_OK;
+}
+
+int ready(const dm_ctx* c)
+{
+    if (c == nullptr) return DM_ERR_ARG;
+    if (c->ws == nullptr) return DM_ERR_STATE;
+    return DM_OK;
+}
+
+int run_pass(dm_ctx* c, int which, uint16_t* labels, long long* lb)
+{
+    dm::DmmArgs a{};
+    uint8_t* ws = c->ws;
+    a.which = which;
+    a.H = c->H;
+    a.W = c->W;
+    a.L = c->L;
+    a.KP = c->KP;
+    a.cost = ws + c->lay.cost;
+    int32_t* lh = reinterpret_cast<int32_t*>(ws + c->lay.lam_h);
+    int32_t* lv = reinterpret_cast<int32_t*>(ws + c->lay.lam_v);
+    a.lam_in = which == 0 ? lv : lh;
+    a.lam_out = which == 0 ? lh : lv;
+    a.wedge = ws + (which == 0 ? c->lay.wh : c->lay.wv);
+    a.fmsg = reinterpret_cast<int32_t*>(ws + c->lay.fmsg);
+    a.bmsg = reinterpret_cast<int32_t*>(ws + c->lay.bmsg);
+    a.taps = reinterpret_cast<const int32_t*>(ws + c->lay.taps);
+    a.err = reinterpret_cast<int32_t*>(ws + c->lay.err);
+    a.labels = labels;
+    a.lb = lb;
+    DM_CK(dm::launch_dmm_pass(a, c->lpt, c->radius, c->stream));
+    c->launches += 1;
+    return DM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+DM_API int dm_default_params(dm_params* p)
+{
+    if (p == nullptr) return DM_ERR_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->struct_size = sizeof(dm_params);
+    p->census_win = 5;
+    p->edge_threshold = 16;
+    p->w_hi = 8;
+    p->w_lo = 4;
+    p->eps = 0.25;
+    p->delta = 1.0;
+    p->C = 2.0;
+    p->lambda_r = 1.0;
+    p->alpha = 1.0;
+    p->tau = 0.35;
+    p->sigma = 0.35;
+    p->h = 1.0;
+    p->warps = 5;
+    return DM_OK;
+}
+
+DM_API int dm_create(int H, int W, int L, const dm_params* p, dm_ctx** out)
+{
+    if (out == nullptr || p == nullptr) return DM_ERR_ARG;
+    *out = nullptr;
+    if (H < 1 || W < 1 || L < 2 || L > 256) return DM_ERR_ARG;
+    if ((long long)H * W * L >= (1LL << 31) || H > 65535 || W > 65535) return DM_ERR_ARG;
+    if (!params_ok(*p)) return DM_ERR_ARG;
+    dm_ctx* c = new (std::nothrow) dm_ctx();
+    if (c == nullptr) return DM_ERR_ARG;
+    c->H = H;
+    c->W = W;
+    c->L = L;
+    c->p = *p;
+    c->lpt = L <= 32 ? 1 : (L <= 64 ? 2 : (L <= 128 ? 4 : 8));
+    c->KP = 32 * c->lpt;
+    c->taps.assign(256 * dm::kTapW, 0);
+    int radius = 1;
+    for (int om = 0; om < 256; ++om) {
+        const int r = build_taps(om, L, *p, &c->taps[om * dm::kTapW]);
+        if (r < 0 && (om == p->w_hi || om == p->w_lo)) c->discrete_ok = false;
+        if (r > radius) radius = r;
+    }
+    c->radius = radius;
+    // workspace layout
+    dm::Layout& l = c->lay;
+    size_t tot = 0;
+    auto add = [&](size_t bytes) {
+        const size_t off = align_up(tot, 256);
+        tot = off + bytes;
+        return off;
+    };
+    const size_t HW = (size_t)H * W, HWL = HW * L;
+    l.cost = add(HWL);
+    l.census = add(2 * HW * sizeof(uint32_t));
+    l.img = add(2 * HW);
+    l.wh = add(HW);
+    l.wv = add(HW);
+    l.lam_h = add(HWL * sizeof(int32_t));
+    l.lam_v = add(HWL * sizeof(int32_t));
+    l.fmsg = add(HW * c->KP * sizeof(int32_t));
+    l.bmsg = add(HW * c->KP * sizeof(int32_t));
+    l.labels = add(HW * sizeof(uint16_t));
+    l.lb = add(kMaxIters * sizeof(long long));
+    l.taps = add(256 * dm::kTapW * sizeof(int32_t));
+    l.u = add(HW * 4);
+    l.u_new = add(HW * 4);
+    l.u0 = add(HW * 4);
+    l.s1 = add(HW * 4);
+    l.s2 = add(HW * 4);
+    l.lo = add(HW * 4);
+    l.hi = add(HW * 4);
+    l.ph = add(HW * 4);
+    l.pv = add(HW * 4);
+    l.qh = add(HW * 4);
+    l.qv = add(HW * 4);
+    l.epart = add(1024 * sizeof(double));
+    l.err = add(sizeof(int32_t));
+    l.total = align_up(tot, 256);
+    *out = c;
+    return DM_OK;
+}
+
+DM_API int dm_destroy(dm_ctx* ctx)
+{
+    delete ctx;
+    return DM_OK;
+}
+
+DM_API int dm_workspace_bytes(const dm_ctx* ctx, size_t* bytes)
+{
+    if (ctx == nullptr || bytes == nullptr) return DM_ERR_ARG;
+    *bytes = ctx->lay.total;
+    return DM_OK;
+}
+
+DM_API int dm_bind_workspace(dm_ctx* ctx, void* d_workspace, size_t bytes)
+{
+    if (ctx == nullptr || d_workspace == nullptr) return DM_ERR_ARG;
+    if (bytes < ctx->lay.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255) != 0)
+        return DM_ERR_WORKSPACE;
+    ctx->ws = static_cast<uint8_t*>(d_workspace);
+    ctx->ws_bytes = bytes;
+    ctx->have_cost = ctx->have_labels = ctx->have_u = false;
+    ctx->u_cur = 0;
+    ctx->last_iters = 0;
+    DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.taps, ctx->taps.data(),
+                          ctx->taps.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    DM_CK(cudaMemsetAsync(ctx->ws + ctx->lay.err, 0, sizeof(int32_t), ctx->stream));
+    DM_CK(cudaStreamSynchronize(ctx->stream));
+    return DM_OK;
+}
+
+DM_API int dm_set_stream(dm_ctx* ctx, void* stream)
+{
+    if (ctx == nullptr) return DM_ERR_ARG;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return DM_OK;
+}
+
+DM_API int dm_reset_duals(dm_ctx* ctx)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    const size_t HWL = (size_t)ctx->H * ctx->W * ctx->L;
+    DM_CK(cudaMemsetAsync(ctx->ws + ctx->lay.lam_v, 0, HWL * sizeof(int32_t), ctx->stream));
+    DM_CK(cudaMemsetAsync(ctx->ws + ctx->lay.lam_h, 0, HWL * sizeof(int32_t), ctx->stream));
+    ctx->have_labels = false;
+    return DM_OK;
+}
+
+DM_API int dm_cost_volume(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (d_left == nullptr || d_right == nullptr) return DM_ERR_ARG;
+    uint8_t* ws = ctx->ws;
+    uint32_t* census = reinterpret_cast<uint32_t*>(ws + ctx->lay.census);
+    DM_CK(dm::launch_census_edges(d_left, d_right, ctx->H, ctx->W, ctx->p.census_win,
+                                  ctx->p.edge_threshold, ctx->p.w_hi, ctx->p.w_lo, census,
+                                  ws + ctx->lay.wh, ws + ctx->lay.wv, ctx->stream));
+    DM_CK(dm::launch_cost(census, ctx->H, ctx->W, ctx->L,
+                          ctx->p.census_win * ctx->p.census_win - 1, ws + ctx->lay.cost,
+                          ctx->stream));
+    ctx->launches += 2;
+    ctx->have_cost = true;
+    return dm_reset_duals(ctx);
+}
+
+DM_API int dm_set_cost_volume(dm_ctx* ctx, const uint8_t* d_cost, const uint8_t* d_wh,
+                              const uint8_t* d_wv)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (d_cost == nullptr || d_wh == nullptr || d_wv == nullptr) return DM_ERR_ARG;
+    const size_t HW = (size_t)ctx->H * ctx->W;
+    DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.cost, d_cost, HW * ctx->L, cudaMemcpyDeviceToDevice,
+                          ctx->stream));
+    DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.wh, d_wh, HW, cudaMemcpyDeviceToDevice, ctx->stream));
+    DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.wv, d_wv, HW, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->have_cost = true;
+    return dm_reset_duals(ctx);
+}
+
+DM_API int dm_discrete_pass(dm_ctx* ctx, int which)
+{
+    if (ctx == nullptr || (which != 0 && which != 1) || !ctx->discrete_ok) return DM_ERR_ARG;
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (!ctx->have_cost) return DM_ERR_STATE;
+    return run_pass(ctx, which, nullptr, nullptr);
+}
+
+DM_API int dm_discrete(dm_ctx* ctx, int iters, int64_t* h_lb)
+{
+    if (ctx == nullptr || iters < 1 || iters > kMaxIters || !ctx->discrete_ok) return DM_ERR_ARG;
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (!ctx->have_cost) return DM_ERR_STATE;
+    long long* lb = reinterpret_cast<long long*>(ctx->ws + ctx->lay.lb);
+    uint16_t* labels = reinterpret_cast<uint16_t*>(ctx->ws + ctx->lay.labels);
+    DM_CK(cudaMemsetAsync(lb, 0, iters * sizeof(long long), ctx->stream));
+    for (int t = 0; t < iters; ++t) {
+        if ((rc = run_pass(ctx, 0, nullptr, nullptr))) return rc;
+        if ((rc = run_pass(ctx, 1, t == iters - 1 ? labels : nullptr, lb + t))) return rc;
+    }
+    ctx->have_labels = true;
+    ctx->last_iters = iters;
+    if (h_lb != nullptr) {
+        DM_CK(cudaMemcpyAsync(h_lb, lb, iters * sizeof(long long), cudaMemcpyDeviceToHost,
+                              ctx->stream));
+        return check_device_error(ctx);
+    }
+    return DM_OK;
+}
+
+DM_API int dm_refine(dm_ctx* ctx, int iters, const float* d_u0)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (iters < 0) return DM_ERR_ARG;
+    if (!ctx->have_cost) return DM_ERR_STATE;
+    if (d_u0 == nullptr && !ctx->have_labels) return DM_ERR_STATE;
+    const int n = ctx->H * ctx->W;
+    ctx->u_cur = 0;
+    dm::PdArgs a = pd_args(ctx);
+    if (d_u0 != nullptr)
+        DM_CK(cudaMemcpyAsync(a.u, d_u0, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+        DM_CK(dm::launch_init_u_from_labels(
+            reinterpret_cast<const uint16_t*>(ctx->ws + ctx->lay.labels), a.u, n, ctx->stream));
+    for (float* s : {a.ph, a.pv, a.qh, a.qv}) DM_CK(dm::launch_zero_f32(s, n, ctx->stream));
+    ctx->launches += (d_u0 != nullptr ? 0 : 1) + 4;
+    const int warps = ctx->p.warps;
+    const int base = iters / warps, extra = iters % warps;
+    for (int w = 0; w < warps; ++w) {
+        const int nit = base + (w < extra ? 1 : 0);
+        a = pd_args(ctx);
+        DM_CK(dm::launch_linearise(a, ctx->stream));
+        ctx->launches += 1;
+        for (int it = 0; it < nit; ++it) {
+            a = pd_args(ctx);
+            DM_CK(dm::launch_pd_iter(a, ctx->stream));
+            ctx->launches += 2;
+            ctx->u_cur ^= 1;
+        }
+    }
+    ctx->have_u = true;
+    return DM_OK;
+}
+
+DM_API int dm_get_labels(dm_ctx* ctx, uint16_t* d_labels)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (d_labels == nullptr) return DM_ERR_ARG;
+    if (!ctx->have_labels) return DM_ERR_STATE;
+    DM_CK(cudaMemcpyAsync(d_labels, ctx->ws + ctx->lay.labels,
+                          (size_t)ctx->H * ctx->W * sizeof(uint16_t), cudaMemcpyDeviceToDevice,
+                          ctx->stream));
+    return DM_OK;
+}
+
+DM_API int dm_get_disparity(dm_ctx* ctx, float* d_u)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (d_u == nullptr) return DM_ERR_ARG;
+    if (!ctx->have_u) return DM_ERR_STATE;
+    dm::PdArgs a = pd_args(ctx);
+    DM_CK(cudaMemcpyAsync(d_u, a.u, (size_t)ctx->H * ctx->W * sizeof(float),
+                          cudaMemcpyDeviceToDevice, ctx->stream));
+    return DM_OK;
+}
+
+DM_API int dm_get_duals(dm_ctx* ctx, int32_t* d_lam_h, int32_t* d_lam_v)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    const size_t bytes = (size_t)ctx->H * ctx->W * ctx->L * sizeof(int32_t);
+    if (d_lam_h)
+        DM_CK(cudaMemcpyAsync(d_lam_h, ctx->ws + ctx->lay.lam_h, bytes, cudaMemcpyDeviceToDevice,
+                              ctx->stream));
+    if (d_lam_v)
+        DM_CK(cudaMemcpyAsync(d_lam_v, ctx->ws + ctx->lay.lam_v, bytes, cudaMemcpyDeviceToDevice,
+                              ctx->stream));
+    return DM_OK;
+}
+
+DM_API int dm_get_cost_volume(dm_ctx* ctx, uint8_t* d_cost, uint8_t* d_wh, uint8_t* d_wv)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (!ctx->have_cost) return DM_ERR_STATE;
+    const size_t HW = (size_t)ctx->H * ctx->W;
+    if (d_cost)
+        DM_CK(cudaMemcpyAsync(d_cost, ctx->ws + ctx->lay.cost, HW * ctx->L,
+                              cudaMemcpyDeviceToDevice, ctx->stream));
+    if (d_wh)
+        DM_CK(cudaMemcpyAsync(d_wh, ctx->ws + ctx->lay.wh, HW, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (d_wv)
+        DM_CK(cudaMemcpyAsync(d_wv, ctx->ws + ctx->lay.wv, HW, cudaMemcpyDeviceToDevice, ctx->stream));
+    return DM_OK;
+}
+
+DM_API int dm_get_lower_bounds(dm_ctx* ctx, int64_t* h_lb, int n)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (h_lb == nullptr || n < 0 || n > ctx->last_iters) return DM_ERR_ARG;
+    if (n > 0)
+        DM_CK(cudaMemcpyAsync(h_lb, ctx->ws + ctx->lay.lb, n * sizeof(int64_t),
+                              cudaMemcpyDeviceToHost, ctx->stream));
+    return check_device_error(ctx);
+}
+
+DM_API int dm_energy(dm_ctx* ctx, double* h_energy)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (h_energy == nullptr) return DM_ERR_ARG;
+    if (!ctx->have_u) return DM_ERR_STATE;
+    dm::PdArgs a = pd_args(ctx);
+    const int nb = dm::energy_blocks(ctx->H, ctx->W);
+    double* part = reinterpret_cast<double*>(ctx->ws + ctx->lay.epart);
+    DM_CK(dm::launch_energy(a, ctx->p.eps, ctx->p.delta, ctx->p.C, part, nb, ctx->stream));
+    ctx->launches += 1;
+    std::vector<double> host(nb);
+    DM_CK(cudaMemcpyAsync(host.data(), part, nb * sizeof(double), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+    DM_CK(cudaStreamSynchronize(ctx->stream));
+    double e = 0.0;
+    for (int b = 0; b < nb; ++b) e += host[b];
+    *h_energy = e;
+    return check_device_error(ctx);
+}
+
+DM_API int dm_solve(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int dmm_iters,
+                    int pd_iters, float* d_u)
+{
+    int rc;
+    if ((rc = dm_cost_volume(ctx, d_left, d_right))) return rc;
+    if ((rc = dm_discrete(ctx, dmm_iters, nullptr))) return rc;
+    if ((rc = dm_refine(ctx, pd_iters, nullptr))) return rc;
+    if (d_u != nullptr && (rc = dm_get_disparity(ctx, d_u))) return rc;
+    return DM_OK;
+}
+
+DM_API int dm_solve_host(dm_ctx* ctx, const uint8_t* h_left, const uint8_t* h_right,
+                         int dmm_iters, int pd_iters, float* h_u, uint16_t* h_labels)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (h_left == nullptr || h_right == nullptr || h_u == nullptr) return DM_ERR_ARG;
+    const size_t HW = (size_t)ctx->H * ctx->W;
+    uint8_t* dimg = ctx->ws + ctx->lay.img;
+    DM_CK(cudaMemcpyAsync(dimg, h_left, HW, cudaMemcpyHostToDevice, ctx->stream));
+    DM_CK(cudaMemcpyAsync(dimg + HW, h_right, HW, cudaMemcpyHostToDevice, ctx->stream));
+    if ((rc = dm_solve(ctx, dimg, dimg + HW, dmm_iters, pd_iters, nullptr))) return rc;
+    dm::PdArgs a = pd_args(ctx);
+    DM_CK(cudaMemcpyAsync(h_u, a.u, HW * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    if (h_labels != nullptr)
+        DM_CK(cudaMemcpyAsync(h_labels, ctx->ws + ctx->lay.labels, HW * sizeof(uint16_t),
+                              cudaMemcpyDeviceToHost, ctx->stream));
+    return check_device_error(ctx);
+}
+
+DM_API int dm_launch_count(const dm_ctx* ctx, uint64_t* count)
+{
+    if (ctx == nullptr || count == nullptr) return DM_ERR_ARG;
+    *count = ctx->launches;
+    return DM_OK;
+}
+
+DM_API int dm_sync(dm_ctx* ctx)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    return check_device_error(ctx);
+}
+
+DM_API const char* dm_error_string(int status)
+{
+    switch (status) {
+        case DM_OK: return "ok";
+        case DM_ERR_ARG: return "invalid argument";
+        case DM_ERR_CUDA: return "CUDA runtime error";
+        case DM_ERR_RANGE: return "value out of range for its storage type";
+        case DM_ERR_TIMEOUT: return "bounded device wait timed out";
+        case DM_ERR_STATE: return "invalid call order or missing workspace";
+        case DM_ERR_WORKSPACE: return "workspace too small or misaligned";
+        case DM_ERR_DEVICE: return "a kernel flagged invalid input data";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal declarations shared by the CUDA translation units of libdm.so.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/dm.h"
+
+namespace dm {
+
+// Penalty taps per edge weight omega (0..255): row = [T_1 .. T_RMAX, P2, valid, pad, pad].
+// T_d = omega * r(d) for d = 1..RMAX (capped at P2), P2 = omega * C is the
+// truncation; the sampled pairwise table is V(0) = 0, V(d) = T_d for d <= RMAX,
+// V(d) = P2 beyond.
+constexpr int kRMax = 4;
+constexpr int kTapW = 8;
+constexpr int kTapP2 = kRMax;
+constexpr int kTapValid = kRMax + 1;
+
+// A value that never wins a minimisation and cannot overflow when two of them
+// and a few penalties are added in int32.
+constexpr int kInf = 1 << 29;
+
+// device-side error codes written to the workspace error word
+constexpr int kDevErrBadOmega = 1;
+
+struct Layout {
+    size_t cost, census, img, wh, wv, lam_h, lam_v, fmsg, bmsg, labels, lb, taps;
+    size_t u, u_new, u0, s1, s2, lo, hi, ph, pv, qh, qv, epart, err;
+    size_t total;
+};
+
+struct DmmArgs {
+    int which;              // 0 horizontal chains (rows), 1 vertical chains (columns)
+    int H, W, L, KP;        // KP: labels padded to 32 * LPT
+    const uint8_t* cost;    // [H][W][L]
+    const int32_t* lam_in;  // lambda_v (which = 0) or lambda_h (which = 1)
+    int32_t* lam_out;       // lambda_h (which = 0) or lambda_v (which = 1)
+    const uint8_t* wedge;   // wh (which = 0) or wv (which = 1)
+    int32_t* fmsg;          // [chains][n][KP] scratch: messages entering from the left
+    int32_t* bmsg;          // [chains][n][KP] scratch: messages entering from the right
+    const int32_t* taps;    // [256][kTapW]
+    int32_t* err;
+    // finalisation (last vertical pass of a dm_discrete call)
+    uint16_t* labels;       // nullable: per-pixel argmin of lambda_h + lambda_v
+    long long* lb;          // nullable: sum_i min_l (lambda_h + lambda_v)_i(l)
+};
+
+struct PdArgs {
+    int H, W, L;
+    const uint8_t* cost;
+    const uint8_t* wh;
+    const uint8_t* wv;
+    float alpha, lambda_r, tau, sigma, h;
+    float ap, bp, bq;       // (alpha, beta) of R+, beta of R-
+    float* u;
+    float* u_new;
+    float* u0;
+    float* s1;
+    float* s2;
+    float* lo;
+    float* hi;
+    float* ph;
+    float* pv;
+    float* qh;
+    float* qv;
+};
+
+// cost.cu
+cudaError_t launch_census_edges(const uint8_t* left, const uint8_t* right, int H, int W, int win,
+                                int T, int w_hi, int w_lo, uint32_t* census, uint8_t* wh,
+                                uint8_t* wv, cudaStream_t s);
+cudaError_t launch_cost(const uint32_t* census, int H, int W, int L, int maxc, uint8_t* cost,
+                        cudaStream_t s);
+
+// dmm.cu
+cudaError_t launch_dmm_pass(const DmmArgs& a, int lpt, int radius, cudaStream_t s);
+
+// pd.cu
+cudaError_t launch_init_u_from_labels(const uint16_t* labels, float* u, int n, cudaStream_t s);
+cudaError_t launch_linearise(const PdArgs& a, cudaStream_t s);
+cudaError_t launch_pd_iter(const PdArgs& a, cudaStream_t s);
+cudaError_t launch_zero_f32(float* p, size_t n, cudaStream_t s);
+cudaError_t launch_energy(const PdArgs& a, double eps, double delta, double C, double* partial,
+                          int nblocks, cudaStream_t s);
+int energy_blocks(int H, int W);
+
+}  // namespace dm

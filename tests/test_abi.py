@@ -1,0 +1,101 @@
+"""The C ABI library builds, loads and exports every symbol of include/dm.h;
+host-side argument checking works without a GPU (no compute call is made)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1601_06274_gb300 import build, dm
+    build.build()
+    return dm.lib()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "dm.h")).read()
+    return re.findall(r"DM_API\s+[\w\s\*]+?\b(dm_\w+)\s*\(", src)
+
+
+def test_header_declares_the_boundary():
+    names = set(declared_symbols())
+    for required in ("dm_create", "dm_cost_volume", "dm_discrete", "dm_refine", "dm_solve"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_default_params_and_create(lib):
+    from paper_1601_06274_gb300 import dm
+    p = dm.default_params()
+    assert p.struct_size == ctypes.sizeof(dm.DmParams)
+    assert (p.census_win, p.w_hi, p.w_lo, p.eps, p.delta, p.C, p.warps) == (5, 8, 4, 0.25, 1.0, 2.0, 5)
+    h = ctypes.c_void_p()
+    assert lib.dm_create(375, 1242, 128, ctypes.byref(p), ctypes.byref(h)) == 0
+    nbytes = ctypes.c_size_t()
+    assert lib.dm_workspace_bytes(h, ctypes.byref(nbytes)) == 0
+    # cost volume + two int32 duals + two message scratches dominate
+    assert nbytes.value >= 375 * 1242 * 128 * (1 + 4 * 4)
+    assert lib.dm_destroy(h) == 0
+
+
+@pytest.mark.parametrize("H,W,L,field,value", [
+    (0, 10, 16, None, None), (10, 0, 16, None, None), (10, 10, 1, None, None),
+    (10, 10, 257, None, None), (10, 10, 16, "census_win", 7), (10, 10, 16, "w_hi", 256),
+    (10, 10, 16, "tau", 0.0), (10, 10, 16, "warps", 0), (10, 10, 16, "struct_size", 8),
+    (10, 10, 16, "C", -1.0),
+])
+def test_create_rejects_invalid_arguments(lib, H, W, L, field, value):
+    from paper_1601_06274_gb300 import dm
+    p = dm.default_params()
+    if field is not None:
+        setattr(p, field, value)
+    h = ctypes.c_void_p()
+    assert lib.dm_create(H, W, L, ctypes.byref(p), ctypes.byref(h)) == dm.DM_ERR_ARG
+    assert not h.value
+
+
+@pytest.mark.parametrize("field,value", [("w_hi", 3), ("C", 9.0), ("eps", 0.3)])
+def test_penalty_without_integer_taps_disables_discrete_stage(lib, field, value):
+    # 3 * 1/4 is not an integer; C = 9 does not reach the cap within 4 labels
+    from paper_1601_06274_gb300 import dm
+    p = dm.default_params()
+    setattr(p, field, value)
+    h = ctypes.c_void_p()
+    assert lib.dm_create(10, 10, 16, ctypes.byref(p), ctypes.byref(h)) == 0
+    assert lib.dm_discrete(h, 1, None) == dm.DM_ERR_ARG
+    assert lib.dm_discrete_pass(h, 0) == dm.DM_ERR_ARG
+    assert lib.dm_refine(h, 1, None) == dm.DM_ERR_STATE  # no workspace yet, but allowed
+    lib.dm_destroy(h)
+
+
+def test_calls_without_workspace_are_state_errors(lib):
+    from paper_1601_06274_gb300 import dm
+    p = dm.default_params()
+    h = ctypes.c_void_p()
+    assert lib.dm_create(8, 8, 16, ctypes.byref(p), ctypes.byref(h)) == 0
+    assert lib.dm_discrete(h, 1, None) == dm.DM_ERR_STATE
+    assert lib.dm_refine(h, 1, None) == dm.DM_ERR_STATE
+    assert lib.dm_cost_volume(h, None, None) == dm.DM_ERR_STATE
+    assert lib.dm_bind_workspace(h, ctypes.c_void_p(4096 + 8), 1 << 30) == dm.DM_ERR_WORKSPACE
+    assert lib.dm_bind_workspace(h, ctypes.c_void_p(4096), 16) == dm.DM_ERR_WORKSPACE
+    assert lib.dm_discrete(None, 1, None) == dm.DM_ERR_ARG
+    lib.dm_destroy(h)
+
+
+def test_error_strings(lib):
+    from paper_1601_06274_gb300 import dm
+    assert dm.error_string(0) == "ok"
+    for code in range(1, 8):
+        assert dm.error_string(code) not in ("ok", "unknown status")
+    assert dm.error_string(99) == "unknown status"
