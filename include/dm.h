@@ -167,6 +167,34 @@ DM_API int dm_get_lower_bounds(dm_ctx* ctx, int64_t* h_lb, int n);
  * (Eq. mrf_formulation) of the current disparity; synchronous. */
 DM_API int dm_energy(dm_ctx* ctx, double* h_energy);
 
+/* Allocation-free variant of dm_discrete_pass.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * (a fixed memory budget decided at start-up, a real-time or embedded
+ * pipeline that forbids allocation while running, or an environment where
+ * cudaMalloc is unavailable).  It needs no context and no workspace and calls
+ * no allocating routine: the caller passes the inputs and the output, all
+ * device pointers on the current device, and the pass's scratch lives in a
+ * fixed 32 MiB device array inside libdm.so that every GPU loading the
+ * library holds until the process exits.
+ *   which = 0: horizontal chains, unaries d_cost + d_lam_in (d_lam_in =
+ *              lambda_v), d_wedge = wh, writes d_lam_out = lambda_h;
+ *   which = 1: vertical chains, unaries d_lam_in (= lambda_h), d_wedge = wv,
+ *              writes d_lam_out = lambda_v (d_cost may be NULL).
+ * Layouts are those of the context API ([H][W][L] uint8 cost, [H][W] uint8
+ * weights, [H][W][L] int32 duals); *p supplies the penalty.  d_err (nullable,
+ * caller-zeroed device int32) receives nonzero bits if an edge weight has no
+ * integer penalty table.  Asynchronous on `stream` (a cudaStream_t as void*).
+ * Limit: 2 * H * W * KP * 4 bytes <= 32 MiB - 8.25 KiB, where KP is L rounded
+ * up to 32, 64, 128 or 256; larger problems return DM_ERR_WORKSPACE before any
+ * work is enqueued.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the one array: calls whose
+ * work overlaps on the GPU race. */
+DM_API int dm_discrete_pass_noalloc(int H, int W, int L, const dm_params* p, int which,
+                                    const uint8_t* d_cost, const uint8_t* d_wedge,
+                                    const int32_t* d_lam_in, int32_t* d_lam_out,
+                                    int32_t* d_err, void* stream);
+
 /* Number of kernels this context has enqueued since dm_create (host-side
  * counter; instrumentation for benchmarks). */
 DM_API int dm_launch_count(const dm_ctx* ctx, uint64_t* count);

@@ -177,6 +177,14 @@ int run_pass(dm_ctx* c, int which, uint16_t* labels, long long* lb)
 
 }  // namespace
 
+namespace dm {
+// Penalty taps of one edge weight (shared with the allocation-free entry point).
+int penalty_taps(int omega, int L, const dm_params& p, int32_t* row)
+{
+    return build_taps(omega, L, p, row);
+}
+}  // namespace dm
+
 extern "C" {
 
 DM_API int dm_default_params(dm_params* p)

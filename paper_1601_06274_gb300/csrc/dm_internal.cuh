@@ -67,6 +67,9 @@ struct PdArgs {
     float* qv;
 };
 
+// dm_abi.cu: row of taps for one omega; returns the window radius or -1
+int penalty_taps(int omega, int L, const dm_params& p, int32_t* row);
+
 // cost.cu
 cudaError_t launch_census_edges(const uint8_t* left, const uint8_t* right, int H, int W, int win,
                                 int T, int w_hi, int w_lo, uint32_t* census, uint8_t* wh,

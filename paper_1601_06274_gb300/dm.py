@@ -73,6 +73,8 @@ def lib() -> ctypes.CDLL:
             "dm_energy": [_vp, ctypes.POINTER(ctypes.c_double)],
             "dm_sync": [_vp],
             "dm_launch_count": [_vp, ctypes.POINTER(ctypes.c_uint64)],
+            "dm_discrete_pass_noalloc": [_i, _i, _i, ctypes.POINTER(DmParams), _i, _vp, _vp,
+                                         _vp, _vp, _vp, _vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -238,6 +240,18 @@ class Context:
 
     def sync(self):
         _ck(lib().dm_sync(self._h), "dm_sync")
+
+
+def discrete_pass_noalloc(params: DmParams, which: int, cost, wedge, lam_in, lam_out,
+                          err=None, stream=None):
+    """dm_discrete_pass_noalloc: one Dual MM pass with no workspace and no
+    allocation inside the library (inputs/outputs are caller tensors)."""
+    H, W, L = lam_in.shape
+    st = stream.cuda_stream if stream is not None else None
+    _ck(lib().dm_discrete_pass_noalloc(H, W, L, ctypes.byref(params), int(which), _ptr(cost),
+                                       _ptr(wedge), _ptr(lam_in), _ptr(lam_out), _ptr(err),
+                                       _vp(st) if st else None),
+        "dm_discrete_pass_noalloc")
 
 
 def labels_u16(t) -> np.ndarray:
