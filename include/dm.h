@@ -81,7 +81,10 @@ typedef struct dm_params {
     double tau, sigma;      /* primal and dual step sizes (Eq. cont_iterates)    */
     double h;               /* linearisation half-width in labels (Sec. 3.1)    */
     int32_t warps;          /* re-linearisations of the data term (Sec. 3.1)    */
-    int32_t reserved[7];
+    int32_t dmm_path;       /* Dual MM kernel: 0 = automatic (packed 16-bit     */
+                            /* arithmetic whenever its value bounds hold),       */
+                            /* 1 = always the int32 kernel                       */
+    int32_t reserved[6];
 } dm_params;
 
 typedef struct dm_ctx dm_ctx;

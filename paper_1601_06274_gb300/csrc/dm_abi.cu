@@ -12,6 +12,15 @@
 struct dm_ctx {
     int H = 0, W = 0, L = 0, KP = 0, lpt = 0, radius = 1;
     bool discrete_ok = true;    // w_hi and w_lo have integer penalty taps within kRMax
+    // packed 16-bit Dual MM (dmm16.cu): usable when L is a multiple of 2*np16 and
+    // every penalty cap is small; delta_bytes is chosen per cost volume
+    bool can16 = false;
+    bool use16 = false;
+    int np16 = 1;
+    int delta_bytes = 2;
+    int p2_all = 0;             // largest cap omega*C over every usable omega
+    int p2_used = 0;            // largest cap over w_hi, w_lo
+    std::vector<uint32_t> taps16;
     dm_params p{};
     dm::Layout lay{};
     uint8_t* ws = nullptr;
@@ -149,8 +158,62 @@ int ready(const dm_ctx* c)
     return DM_OK;
 }
 
+// packed messages of the 16-bit kernel: 32 * np16 uint32 per chain node
+size_t msg16_bytes(const dm_ctx* c)
+{
+    return align_up((size_t)c->H * c->W * 32 * c->np16 * sizeof(uint32_t), 256);
+}
+
+size_t base_bytes(const dm_ctx* c) { return align_up((size_t)c->H * c->W * 4, 256); }
+
+int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
+{
+    dm::Dmm16Args a{};
+    uint8_t* ws = c->ws;
+    uint8_t* lh = ws + c->lay.lam_h;
+    uint8_t* lv = ws + c->lay.lam_v;
+    uint8_t* in = which == 0 ? lv : lh;
+    uint8_t* out = which == 0 ? lh : lv;
+    a.which = which;
+    a.H = c->H;
+    a.W = c->W;
+    a.L = c->L;
+    a.cost = ws + c->lay.cost;
+    a.base_in = reinterpret_cast<const int32_t*>(in);
+    a.delta_in = in + base_bytes(c);
+    a.base_out = reinterpret_cast<int32_t*>(out);
+    a.delta_out = out + base_bytes(c);
+    a.wedge = ws + (which == 0 ? c->lay.wh : c->lay.wv);
+    a.fmsg = reinterpret_cast<uint32_t*>(ws + c->lay.fmsg);
+    a.bmsg = reinterpret_cast<uint32_t*>(ws + c->lay.bmsg);
+    a.fofs = reinterpret_cast<int32_t*>(ws + c->lay.fmsg + msg16_bytes(c));
+    a.bofs = reinterpret_cast<int32_t*>(ws + c->lay.bmsg + msg16_bytes(c));
+    a.taps16 = reinterpret_cast<const uint32_t*>(ws + c->lay.taps16);
+    a.err = reinterpret_cast<int32_t*>(ws + c->lay.err);
+    a.labels = labels;
+    a.lb = lb;
+    DM_CK(dm::launch_dmm16_pass(a, c->np16, c->radius, c->delta_bytes, c->stream));
+    c->launches += 1;
+    return DM_OK;
+}
+
+// storage of the duals for a new cost volume whose values are <= cost_max
+int choose_path(dm_ctx* c, int cost_max, bool user_weights)
+{
+    const int p2 = user_weights ? c->p2_all : c->p2_used;
+    c->use16 = c->can16;
+    c->delta_bytes = (cost_max + 2 * (p2 + 1) <= 255) ? 1 : 2;
+    if (!c->discrete_ok) return DM_OK;  // weights only feed the continuous stage
+    DM_CK(dm::launch_validate_edges(c->ws + c->lay.wh, c->ws + c->lay.wv, c->H, c->W,
+                                    reinterpret_cast<const int32_t*>(c->ws + c->lay.taps),
+                                    reinterpret_cast<int32_t*>(c->ws + c->lay.err), c->stream));
+    c->launches += 1;
+    return DM_OK;
+}
+
 int run_pass(dm_ctx* c, int which, uint16_t* labels, long long* lb)
 {
+    if (c->use16) return run_pass16(c, which, labels, lb);
     dm::DmmArgs a{};
     uint8_t* ws = c->ws;
     a.which = which;
@@ -231,6 +294,21 @@ DM_API int dm_create(int H, int W, int L, const dm_params* p, dm_ctx** out)
         if (r > radius) radius = r;
     }
     c->radius = radius;
+    c->np16 = L <= 64 ? 1 : (L <= 128 ? 2 : 4);
+    c->taps16.assign(256 * dm::kTapW, 0u);
+    for (int om = 0; om < 256; ++om) {
+        const int32_t* row = &c->taps[om * dm::kTapW];
+        if (!row[dm::kTapValid]) continue;
+        for (int d = 0; d < dm::kRMax; ++d)
+            c->taps16[om * dm::kTapW + d] = ((uint32_t)row[d] & 0xffffu) * 0x10001u;
+        c->taps16[om * dm::kTapW + dm::kTapP2] = (uint32_t)row[dm::kTapP2];
+        c->taps16[om * dm::kTapW + dm::kTapValid] = 1u;
+        if (row[dm::kTapP2] > c->p2_all) c->p2_all = row[dm::kTapP2];
+        if ((om == p->w_hi || om == p->w_lo) && row[dm::kTapP2] > c->p2_used)
+            c->p2_used = row[dm::kTapP2];
+    }
+    c->can16 = c->discrete_ok && p->dmm_path == 0 && (L % (2 * c->np16)) == 0 &&
+               c->p2_all <= 8000;
     // workspace layout
     dm::Layout& l = c->lay;
     size_t tot = 0;
@@ -247,11 +325,16 @@ DM_API int dm_create(int H, int W, int L, const dm_params* p, dm_ctx** out)
     l.wv = add(HW);
     l.lam_h = add(HWL * sizeof(int32_t));
     l.lam_v = add(HWL * sizeof(int32_t));
-    l.fmsg = add(HW * c->KP * sizeof(int32_t));
-    l.bmsg = add(HW * c->KP * sizeof(int32_t));
+    // message scratch: int32 messages of the int32 kernel, or packed messages
+    // plus one int32 offset per node for the 16-bit kernel
+    const size_t msg32 = HW * c->KP * sizeof(int32_t);
+    const size_t msg16 = align_up(HW * 32 * c->np16 * sizeof(uint32_t), 256) + HW * sizeof(int32_t);
+    l.fmsg = add(msg32 > msg16 ? msg32 : msg16);
+    l.bmsg = add(msg32 > msg16 ? msg32 : msg16);
     l.labels = add(HW * sizeof(uint16_t));
     l.lb = add(kMaxIters * sizeof(long long));
     l.taps = add(256 * dm::kTapW * sizeof(int32_t));
+    l.taps16 = add(256 * dm::kTapW * sizeof(uint32_t));
     l.u = add(HW * 4);
     l.u_new = add(HW * 4);
     l.u0 = add(HW * 4);
@@ -295,6 +378,9 @@ DM_API int dm_bind_workspace(dm_ctx* ctx, void* d_workspace, size_t bytes)
     ctx->last_iters = 0;
     DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.taps, ctx->taps.data(),
                           ctx->taps.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.taps16, ctx->taps16.data(),
+                          ctx->taps16.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                          ctx->stream));
     DM_CK(cudaMemsetAsync(ctx->ws + ctx->lay.err, 0, sizeof(int32_t), ctx->stream));
     DM_CK(cudaStreamSynchronize(ctx->stream));
     return DM_OK;
@@ -333,6 +419,7 @@ DM_API int dm_cost_volume(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_r
                           ctx->stream));
     ctx->launches += 2;
     ctx->have_cost = true;
+    if ((rc = choose_path(ctx, ctx->p.census_win * ctx->p.census_win - 1, false))) return rc;
     return dm_reset_duals(ctx);
 }
 
@@ -348,6 +435,7 @@ DM_API int dm_set_cost_volume(dm_ctx* ctx, const uint8_t* d_cost, const uint8_t*
     DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.wh, d_wh, HW, cudaMemcpyDeviceToDevice, ctx->stream));
     DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.wv, d_wv, HW, cudaMemcpyDeviceToDevice, ctx->stream));
     ctx->have_cost = true;
+    if ((rc = choose_path(ctx, 255, true))) return rc;
     return dm_reset_duals(ctx);
 }
 
@@ -447,6 +535,19 @@ DM_API int dm_get_duals(dm_ctx* ctx, int32_t* d_lam_h, int32_t* d_lam_v)
     int rc = ready(ctx);
     if (rc) return rc;
     const size_t bytes = (size_t)ctx->H * ctx->W * ctx->L * sizeof(int32_t);
+    if (ctx->use16) {
+        const long long npx = (long long)ctx->H * ctx->W;
+        const size_t lay[2] = {ctx->lay.lam_h, ctx->lay.lam_v};
+        int32_t* dst[2] = {d_lam_h, d_lam_v};
+        for (int t = 0; t < 2; ++t) {
+            if (dst[t] == nullptr) continue;
+            const uint8_t* reg = ctx->ws + lay[t];
+            DM_CK(dm::launch_duals_to_i32(reinterpret_cast<const int32_t*>(reg), reg + base_bytes(ctx),
+                                          ctx->delta_bytes, npx, ctx->L, dst[t], ctx->stream));
+            ctx->launches += 1;
+        }
+        return DM_OK;
+    }
     if (d_lam_h)
         DM_CK(cudaMemcpyAsync(d_lam_h, ctx->ws + ctx->lay.lam_h, bytes, cudaMemcpyDeviceToDevice,
                               ctx->stream));

@@ -24,9 +24,10 @@ constexpr int kInf = 1 << 29;
 
 // device-side error codes written to the workspace error word
 constexpr int kDevErrBadOmega = 1;
+constexpr int kDevErrRange = 2;
 
 struct Layout {
-    size_t cost, census, img, wh, wv, lam_h, lam_v, fmsg, bmsg, labels, lb, taps;
+    size_t cost, census, img, wh, wv, lam_h, lam_v, fmsg, bmsg, labels, lb, taps, taps16;
     size_t u, u_new, u0, s1, s2, lo, hi, ph, pv, qh, qv, epart, err;
     size_t total;
 };
@@ -45,6 +46,27 @@ struct DmmArgs {
     // finalisation (last vertical pass of a dm_discrete call)
     uint16_t* labels;       // nullable: per-pixel argmin of lambda_h + lambda_v
     long long* lb;          // nullable: sum_i min_l (lambda_h + lambda_v)_i(l)
+};
+
+// Packed 16-bit Dual MM pass (dmm16.cu).  Duals are stored as an int32 base per
+// pixel plus a delta vector ([H][W][L], uint8 or int16); messages as packed
+// int16 pairs ([chains][n][KP/2] uint32) plus an int32 offset ([chains][n]).
+struct Dmm16Args {
+    int which, H, W, L;
+    const uint8_t* cost;
+    const int32_t* base_in;
+    const void* delta_in;
+    int32_t* base_out;
+    void* delta_out;
+    const uint8_t* wedge;
+    uint32_t* fmsg;
+    uint32_t* bmsg;
+    int32_t* fofs;
+    int32_t* bofs;
+    const uint32_t* taps16;  // [256][kTapW]: T_1..T_4 in both halves, P2, valid
+    int32_t* err;
+    uint16_t* labels;
+    long long* lb;
 };
 
 struct PdArgs {
@@ -79,6 +101,14 @@ cudaError_t launch_cost(const uint32_t* census, int H, int W, int L, int maxc, u
 
 // dmm.cu
 cudaError_t launch_dmm_pass(const DmmArgs& a, int lpt, int radius, cudaStream_t s);
+
+// dmm16.cu
+cudaError_t launch_dmm16_pass(const Dmm16Args& a, int np, int radius, int delta_bytes,
+                              cudaStream_t s);
+cudaError_t launch_validate_edges(const uint8_t* wh, const uint8_t* wv, int H, int W,
+                                  const int32_t* taps, int32_t* err, cudaStream_t s);
+cudaError_t launch_duals_to_i32(const int32_t* base, const void* delta, int delta_bytes,
+                                long long n_px, int L, int32_t* out, cudaStream_t s);
 
 // pd.cu
 cudaError_t launch_init_u_from_labels(const uint16_t* labels, float* u, int n, cudaStream_t s);

@@ -34,7 +34,7 @@ class DmParams(ctypes.Structure):
                 ("C", ctypes.c_double), ("lambda_r", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("tau", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("h", ctypes.c_double), ("warps", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("dmm_path", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 _lib = None

@@ -87,9 +87,10 @@ def _check_passes(dm, ctx, cost, wh, wv, iters, P):
 
 
 @pytest.mark.parametrize("H,W,L", SHAPES)
-def test_dmm_passes_bit_exact(dm, H, W, L):
+@pytest.mark.parametrize("path", [0, 1])  # packed 16-bit kernel (where eligible) / int32 kernel
+def test_dmm_passes_bit_exact(dm, H, W, L, path):
     left, right = _pair(H, W, L, seed=7 * H + W + L)
-    ctx = _ctx(dm, H, W, L)
+    ctx = _ctx(dm, H, W, L, dmm_path=path)
     ctx.cost_volume(left, right)
     cost = O.cost_volume(left, right, L)
     wh, wv = O.edge_weights(left)
@@ -97,7 +98,8 @@ def test_dmm_passes_bit_exact(dm, H, W, L):
 
 
 @pytest.mark.parametrize("H,W,L", [(9, 14, 16), (5, 40, 64), (12, 8, 128), (3, 5, 200)])
-def test_dmm_passes_extreme_costs_and_weights(dm, H, W, L):
+@pytest.mark.parametrize("path", [0, 1])
+def test_dmm_passes_extreme_costs_and_weights(dm, H, W, L, path):
     # full uint8 cost range and every usable omega (multiples of 4 up to 252)
     rng = np.random.default_rng(H * W * L)
     cost = rng.integers(0, 256, size=(H, W, L)).astype(np.uint8)
@@ -107,7 +109,7 @@ def test_dmm_passes_extreme_costs_and_weights(dm, H, W, L):
     wv = (4 * rng.integers(0, 64, size=(H, W))).astype(np.uint8)
     wh[:, -1] = 0
     wv[-1, :] = 0
-    ctx = _ctx(dm, H, W, L)
+    ctx = _ctx(dm, H, W, L, dmm_path=path)
     ctx.set_cost_volume(cost, wh, wv)
     _check_passes(dm, ctx, cost.astype(np.int32), wh.astype(np.int32), wv.astype(np.int32), 2,
                   O.Params())
@@ -127,10 +129,11 @@ def test_dmm_other_penalties(dm, params):
 
 
 @pytest.mark.parametrize("H,W,L,iters", [(48, 64, 16, 5), (17, 31, 48, 4), (1, 50, 12, 2),
-                                         (40, 1, 12, 2)])
-def test_discrete_labels_and_bounds(dm, H, W, L, iters):
+                                         (40, 1, 12, 2), (30, 70, 128, 3)])
+@pytest.mark.parametrize("path", [0, 1])
+def test_discrete_labels_and_bounds(dm, H, W, L, iters, path):
     left, right = _pair(H, W, L, seed=H + W)
-    ctx = _ctx(dm, H, W, L)
+    ctx = _ctx(dm, H, W, L, dmm_path=path)
     ctx.cost_volume(left, right)
     lb = ctx.discrete(iters, lower_bounds=True)
     labels = dm.labels_u16(ctx.labels())
