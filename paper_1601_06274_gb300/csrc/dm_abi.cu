@@ -192,6 +192,10 @@ int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
     a.err = reinterpret_cast<int32_t*>(ws + c->lay.err);
     a.labels = labels;
     a.lb = lb;
+    const int n = which == 0 ? c->W : c->H;
+    int cap = 1;
+    while (cap < n) cap <<= 1;
+    a.seg_cap = (cap + 1 + 7) & ~7;  // keeps the second array 16-byte aligned
     DM_CK(dm::launch_dmm16_pass(a, c->np16, c->radius, c->delta_bytes, c->stream));
     c->launches += 1;
     return DM_OK;
@@ -299,16 +303,22 @@ DM_API int dm_create(int H, int W, int L, const dm_params* p, dm_ctx** out)
     for (int om = 0; om < 256; ++om) {
         const int32_t* row = &c->taps[om * dm::kTapW];
         if (!row[dm::kTapValid]) continue;
-        for (int d = 0; d < dm::kRMax; ++d)
-            c->taps16[om * dm::kTapW + d] = ((uint32_t)row[d] & 0xffffu) * 0x10001u;
-        c->taps16[om * dm::kTapW + dm::kTapP2] = (uint32_t)row[dm::kTapP2];
-        c->taps16[om * dm::kTapW + dm::kTapValid] = 1u;
+        // packed row: {T1, T2, P2, valid, T3, T4, 0, 0}, taps in both 16-bit halves
+        uint32_t* r16 = &c->taps16[om * dm::kTapW];
+        r16[0] = ((uint32_t)row[0] & 0xffffu) * 0x10001u;
+        r16[1] = ((uint32_t)row[1] & 0xffffu) * 0x10001u;
+        r16[2] = (uint32_t)row[dm::kTapP2];
+        r16[3] = 1u;
+        r16[4] = ((uint32_t)row[2] & 0xffffu) * 0x10001u;
+        r16[5] = ((uint32_t)row[3] & 0xffffu) * 0x10001u;
         if (row[dm::kTapP2] > c->p2_all) c->p2_all = row[dm::kTapP2];
         if ((om == p->w_hi || om == p->w_lo) && row[dm::kTapP2] > c->p2_used)
             c->p2_used = row[dm::kTapP2];
     }
-    c->can16 = c->discrete_ok && p->dmm_path == 0 && (L % (2 * c->np16)) == 0 &&
-               c->p2_all <= 8000;
+    // the 16-bit kernel stages each unary row as four async copies of L/4 bytes
+    // (uint8 deltas) or L/2 bytes (int16), so L must be a multiple of 16
+    c->can16 = c->discrete_ok && p->dmm_path == 0 && (L % 16) == 0 && c->p2_all <= 8000 &&
+               H <= 8192 && W <= 8192;
     // workspace layout
     dm::Layout& l = c->lay;
     size_t tot = 0;
@@ -400,6 +410,14 @@ DM_API int dm_reset_duals(dm_ctx* ctx)
     const size_t HWL = (size_t)ctx->H * ctx->W * ctx->L;
     DM_CK(cudaMemsetAsync(ctx->ws + ctx->lay.lam_v, 0, HWL * sizeof(int32_t), ctx->stream));
     DM_CK(cudaMemsetAsync(ctx->ws + ctx->lay.lam_h, 0, HWL * sizeof(int32_t), ctx->stream));
+    if (ctx->use16 && ctx->have_cost) {
+        // the 16-bit path keeps c + lambda_v in place of lambda_v: c for a cold start
+        uint8_t* reg = ctx->ws + ctx->lay.lam_v;
+        DM_CK(dm::launch_theta_h_init(ctx->ws + ctx->lay.cost, reinterpret_cast<int32_t*>(reg),
+                                      reg + base_bytes(ctx), ctx->delta_bytes,
+                                      (long long)ctx->H * ctx->W, ctx->L, ctx->stream));
+        ctx->launches += 1;
+    }
     ctx->have_labels = false;
     return DM_OK;
 }
@@ -543,7 +561,8 @@ DM_API int dm_get_duals(dm_ctx* ctx, int32_t* d_lam_h, int32_t* d_lam_v)
             if (dst[t] == nullptr) continue;
             const uint8_t* reg = ctx->ws + lay[t];
             DM_CK(dm::launch_duals_to_i32(reinterpret_cast<const int32_t*>(reg), reg + base_bytes(ctx),
-                                          ctx->delta_bytes, npx, ctx->L, dst[t], ctx->stream));
+                                          ctx->delta_bytes, t == 1 ? ctx->ws + ctx->lay.cost : nullptr,
+                                          npx, ctx->L, dst[t], ctx->stream));
             ctx->launches += 1;
         }
         return DM_OK;

@@ -49,8 +49,10 @@ struct DmmArgs {
 };
 
 // Packed 16-bit Dual MM pass (dmm16.cu).  Duals are stored as an int32 base per
-// pixel plus a delta vector ([H][W][L], uint8 or int16); messages as packed
-// int16 pairs ([chains][n][KP/2] uint32) plus an int32 offset ([chains][n]).
+// pixel plus a delta vector ([H][W][L], uint8 or int16): lambda_h itself, and
+// c + lambda_v (the unary of the horizontal pass) in place of lambda_v;
+// messages as packed int16 pairs ([chains][n][32*NP] uint32) plus an int32
+// offset ([chains][n]).
 struct Dmm16Args {
     int which, H, W, L;
     const uint8_t* cost;
@@ -67,6 +69,7 @@ struct Dmm16Args {
     int32_t* err;
     uint16_t* labels;
     long long* lb;
+    int seg_cap;             // entries of each segment-start array: 2^ceil(log2 n) + 1, padded
 };
 
 struct PdArgs {
@@ -108,7 +111,10 @@ cudaError_t launch_dmm16_pass(const Dmm16Args& a, int np, int radius, int delta_
 cudaError_t launch_validate_edges(const uint8_t* wh, const uint8_t* wv, int H, int W,
                                   const int32_t* taps, int32_t* err, cudaStream_t s);
 cudaError_t launch_duals_to_i32(const int32_t* base, const void* delta, int delta_bytes,
-                                long long n_px, int L, int32_t* out, cudaStream_t s);
+                                const uint8_t* cost, long long n_px, int L, int32_t* out,
+                                cudaStream_t s);
+cudaError_t launch_theta_h_init(const uint8_t* cost, int32_t* base, void* delta, int delta_bytes,
+                                long long n_px, int L, cudaStream_t s);
 
 // pd.cu
 cudaError_t launch_init_u_from_labels(const uint16_t* labels, float* u, int n, cudaStream_t s);
