@@ -31,6 +31,7 @@ struct dm_ctx {
     bool have_labels = false;
     bool have_u = false;
     int u_cur = 0;              // 0: current disparity in lay.u, 1: in lay.u_new
+    int pq_cur = 0;             // 0: current p, q in lay.ph.., 1: in lay.ph2..
     int last_iters = 0;
     unsigned long long launches = 0;  // kernels enqueued by this context
 };
@@ -135,10 +136,22 @@ dm::PdArgs pd_args(dm_ctx* c)
     a.s2 = reinterpret_cast<float*>(ws + l.s2);
     a.lo = reinterpret_cast<float*>(ws + l.lo);
     a.hi = reinterpret_cast<float*>(ws + l.hi);
-    a.ph = reinterpret_cast<float*>(ws + l.ph);
-    a.pv = reinterpret_cast<float*>(ws + l.pv);
-    a.qh = reinterpret_cast<float*>(ws + l.qh);
-    a.qv = reinterpret_cast<float*>(ws + l.qv);
+    float* pa[4] = {reinterpret_cast<float*>(ws + l.ph), reinterpret_cast<float*>(ws + l.pv),
+                    reinterpret_cast<float*>(ws + l.qh), reinterpret_cast<float*>(ws + l.qv)};
+    float* pb[4] = {reinterpret_cast<float*>(ws + l.ph2), reinterpret_cast<float*>(ws + l.pv2),
+                    reinterpret_cast<float*>(ws + l.qh2), reinterpret_cast<float*>(ws + l.qv2)};
+    float** in = c->pq_cur == 0 ? pa : pb;
+    float** out = c->pq_cur == 0 ? pb : pa;
+    a.ph = in[0];
+    a.pv = in[1];
+    a.qh = in[2];
+    a.qv = in[3];
+    a.ph2 = out[0];
+    a.pv2 = out[1];
+    a.qh2 = out[2];
+    a.qv2 = out[3];
+    a.costf = nullptr;
+    a.alpha_px = nullptr;
     return a;
 }
 
@@ -356,6 +369,10 @@ DM_API int dm_create(int H, int W, int L, const dm_params* p, dm_ctx** out)
     l.pv = add(HW * 4);
     l.qh = add(HW * 4);
     l.qv = add(HW * 4);
+    l.ph2 = add(HW * 4);
+    l.pv2 = add(HW * 4);
+    l.qh2 = add(HW * 4);
+    l.qv2 = add(HW * 4);
     l.epart = add(1024 * sizeof(double));
     l.err = add(sizeof(int32_t));
     l.total = align_up(tot, 256);
@@ -498,14 +515,16 @@ DM_API int dm_refine(dm_ctx* ctx, int iters, const float* d_u0)
     if (d_u0 == nullptr && !ctx->have_labels) return DM_ERR_STATE;
     const int n = ctx->H * ctx->W;
     ctx->u_cur = 0;
+    ctx->pq_cur = 0;
     dm::PdArgs a = pd_args(ctx);
     if (d_u0 != nullptr)
         DM_CK(cudaMemcpyAsync(a.u, d_u0, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
     else
         DM_CK(dm::launch_init_u_from_labels(
             reinterpret_cast<const uint16_t*>(ctx->ws + ctx->lay.labels), a.u, n, ctx->stream));
-    for (float* s : {a.ph, a.pv, a.qh, a.qv}) DM_CK(dm::launch_zero_f32(s, n, ctx->stream));
-    ctx->launches += (d_u0 != nullptr ? 0 : 1) + 4;
+    for (float* s : {a.ph, a.pv, a.qh, a.qv, a.ph2, a.pv2, a.qh2, a.qv2})
+        DM_CK(dm::launch_zero_f32(s, n, ctx->stream));
+    ctx->launches += (d_u0 != nullptr ? 0 : 1) + 8;
     const int warps = ctx->p.warps;
     const int base = iters / warps, extra = iters % warps;
     for (int w = 0; w < warps; ++w) {
@@ -516,8 +535,9 @@ DM_API int dm_refine(dm_ctx* ctx, int iters, const float* d_u0)
         for (int it = 0; it < nit; ++it) {
             a = pd_args(ctx);
             DM_CK(dm::launch_pd_iter(a, ctx->stream));
-            ctx->launches += 2;
+            ctx->launches += 1;
             ctx->u_cur ^= 1;
+            ctx->pq_cur ^= 1;
         }
     }
     ctx->have_u = true;

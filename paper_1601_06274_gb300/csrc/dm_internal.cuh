@@ -28,7 +28,7 @@ constexpr int kDevErrRange = 2;
 
 struct Layout {
     size_t cost, census, img, wh, wv, lam_h, lam_v, fmsg, bmsg, labels, lb, taps, taps16;
-    size_t u, u_new, u0, s1, s2, lo, hi, ph, pv, qh, qv, epart, err;
+    size_t u, u_new, u0, s1, s2, lo, hi, ph, pv, qh, qv, ph2, pv2, qh2, qv2, epart, err;
     size_t total;
 };
 
@@ -74,7 +74,9 @@ struct Dmm16Args {
 
 struct PdArgs {
     int H, W, L;
-    const uint8_t* cost;
+    const uint8_t* cost;     // [H][W][L] uint8 samples, used when costf is null
+    const float* costf;      // [H][W][L] float32 samples (nullable)
+    const float* alpha_px;   // [H][W] data weights (nullable: alpha)
     const uint8_t* wh;
     const uint8_t* wv;
     float alpha, lambda_r, tau, sigma, h;
@@ -86,10 +88,14 @@ struct PdArgs {
     float* s2;
     float* lo;
     float* hi;
-    float* ph;
+    float* ph;               // p, q of the current iterate
     float* pv;
     float* qh;
     float* qv;
+    float* ph2;              // p, q written by the iteration (ping-pong)
+    float* pv2;
+    float* qh2;
+    float* qv2;
 };
 
 // dm_abi.cu: row of taps for one omega; returns the window radius or -1

@@ -8,29 +8,44 @@
 // Layout: all state is float32 [H][W].  An edge e = (i, j) with j the right
 // (or lower) neighbour is stored at pixel i in *_h (or *_v); (Au)_e = u_i - u_j.
 //
-// One iteration is two kernels (Jacobi in the pixels):
-//   pd_u_kernel : u_new = prox_{tau D~}(u - tau A^T (p - q))          (reads p, q, u)
-//   pd_pq_kernel: q = prox_{tau R-*}(q + tau A u),                      (reads u, u_new)
-//                 p = prox_{sigma R+*}(p + sigma A (2 u_new - u))
-// The host swaps u and u_new after every iteration.
+// One iteration is one kernel (Jacobi in the pixels, ping-pong buffers): a
+// 32x8 tile first computes u+ = prox_{tau D~}(u - tau A^T (p - q)) on the tile
+// and a one-pixel halo to the right and below (from the old p, q), then the
+// edges of the tile:
+//   q+ = prox_{tau R-*}(q + tau A u),  p+ = prox_{sigma R+*}(p + sigma A (2u+ - u)).
+// The cost samples are uint8 (census) or float32 (a caller's cost volume), the
+// data weight a scalar or a per-pixel map.
 
 #include "dm_internal.cuh"
 
 namespace dm {
 namespace {
 
-// D_i(x): linear interpolation of the cost samples with the argument clamped
-// to [0, L-1]
-__device__ __forceinline__ float interp(const uint8_t* __restrict__ c, int L, float x)
+constexpr int kTX = 32, kTY = 8;
+
+__device__ __forceinline__ float cost_at(const PdArgs& A, size_t i)
 {
+    return A.costf != nullptr ? __ldg(A.costf + i) : (float)__ldg(A.cost + i);
+}
+
+// D_i(x): linear interpolation of the cost samples of pixel px with the argument
+// clamped to [0, L-1]
+__device__ __forceinline__ float interp(const PdArgs& A, size_t px, float x)
+{
+    const int L = A.L;
     x = fminf(fmaxf(x, 0.0f), (float)(L - 1));
     int k = (int)floorf(x);
     if (k > L - 2) k = L - 2;
     if (k < 0) k = 0;
     const float t = x - (float)k;
-    const float c0 = (float)__ldg(c + k);
-    const float c1 = (float)__ldg(c + k + 1);
+    const float c0 = cost_at(A, px * L + k);
+    const float c1 = cost_at(A, px * L + k + 1);
     return c0 + t * (c1 - c0);
+}
+
+__device__ __forceinline__ float alpha_at(const PdArgs& A, int i)
+{
+    return A.alpha_px != nullptr ? __ldg(A.alpha_px + i) : A.alpha;
 }
 
 __global__ void init_u_kernel(const uint16_t* __restrict__ labels, float* __restrict__ u, int n)
@@ -53,13 +68,13 @@ __global__ void linearise_kernel(const PdArgs A)
     const int n = A.H * A.W;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint8_t* c = A.cost + (size_t)i * A.L;
     const float u0 = A.u[i];
-    const float d0 = interp(c, A.L, u0);
-    const float dm = interp(c, A.L, u0 - A.h);
-    const float dp = interp(c, A.L, u0 + A.h);
-    float s1 = A.alpha * (d0 - dm) / A.h;
-    float s2 = A.alpha * (dp - d0) / A.h;
+    const float d0 = interp(A, i, u0);
+    const float dm = interp(A, i, u0 - A.h);
+    const float dp = interp(A, i, u0 + A.h);
+    const float al = alpha_at(A, i);
+    float s1 = al * (d0 - dm) / A.h;
+    float s2 = al * (dp - d0) / A.h;
     if (s2 < s1) {
         s1 = 0.5f * (s1 + s2);
         s2 = s1;
@@ -81,11 +96,9 @@ __device__ __forceinline__ float prox_conj(float t, float omega, float a, float 
     return fminf(fmaxf(v, -omega), omega);
 }
 
-__global__ void pd_u_kernel(const PdArgs A)
+// u+ at pixel (x, y) from the old state
+__device__ __forceinline__ float u_step(const PdArgs& A, int x, int y)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= A.W || y >= A.H) return;
     const int W = A.W;
     const int i = y * W + x;
     float div = 0.0f;  // (A^T (p - q))_i
@@ -101,31 +114,45 @@ __global__ void pd_u_kernel(const PdArgs A)
     if (uh > u0 + ts2) v = uh - ts2;
     else if (uh < u0 + ts1) v = uh - ts1;
     else v = u0;
-    A.u_new[i] = fminf(fmaxf(v, A.lo[i]), A.hi[i]);
+    return fminf(fmaxf(v, A.lo[i]), A.hi[i]);
 }
 
-__global__ void pd_pq_kernel(const PdArgs A)
+__global__ void __launch_bounds__(kTX * kTY) pd_fused_kernel(const PdArgs A)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= A.W || y >= A.H) return;
-    const int W = A.W;
+    __shared__ float s_un[kTY + 1][kTX + 1];  // u+ on the tile and its right/lower halo
+    __shared__ float s_u[kTY + 1][kTX + 1];   // old u there
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int W = A.W, H = A.H;
+    for (int t = threadIdx.x; t < (kTX + 1) * (kTY + 1); t += kTX * kTY) {
+        const int lx = t % (kTX + 1), ly = t / (kTX + 1);
+        const int x = x0 + lx, y = y0 + ly;
+        if (x < W && y < H) {
+            s_un[ly][lx] = u_step(A, x, y);
+            s_u[ly][lx] = A.u[y * W + x];
+        }
+    }
+    __syncthreads();
+    const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x >= W || y >= H) return;
     const int i = y * W + x;
-    const float ui = A.u[i];
-    const float ei = 2.0f * A.u_new[i] - ui;
+    const float ui = s_u[ly][lx];
+    const float uni = s_un[ly][lx];
+    A.u_new[i] = uni;
+    const float ei = 2.0f * uni - ui;
     if (x + 1 < W) {
         const float om = A.lambda_r * (float)A.wh[i];
-        const float uj = A.u[i + 1];
-        const float ej = 2.0f * A.u_new[i + 1] - uj;
-        A.qh[i] = prox_conj(A.qh[i] + A.tau * (ui - uj), om, 0.0f, A.bq, A.tau);
-        A.ph[i] = prox_conj(A.ph[i] + A.sigma * (ei - ej), om, A.ap, A.bp, A.sigma);
+        const float uj = s_u[ly][lx + 1];
+        const float ej = 2.0f * s_un[ly][lx + 1] - uj;
+        A.qh2[i] = prox_conj(A.qh[i] + A.tau * (ui - uj), om, 0.0f, A.bq, A.tau);
+        A.ph2[i] = prox_conj(A.ph[i] + A.sigma * (ei - ej), om, A.ap, A.bp, A.sigma);
     }
-    if (y + 1 < A.H) {
+    if (y + 1 < H) {
         const float om = A.lambda_r * (float)A.wv[i];
-        const float uj = A.u[i + W];
-        const float ej = 2.0f * A.u_new[i + W] - uj;
-        A.qv[i] = prox_conj(A.qv[i] + A.tau * (ui - uj), om, 0.0f, A.bq, A.tau);
-        A.pv[i] = prox_conj(A.pv[i] + A.sigma * (ei - ej), om, A.ap, A.bp, A.sigma);
+        const float uj = s_u[ly + 1][lx];
+        const float ej = 2.0f * s_un[ly + 1][lx] - uj;
+        A.qv2[i] = prox_conj(A.qv[i] + A.tau * (ui - uj), om, 0.0f, A.bq, A.tau);
+        A.pv2[i] = prox_conj(A.pv[i] + A.sigma * (ei - ej), om, A.ap, A.bp, A.sigma);
     }
 }
 
@@ -150,7 +177,7 @@ __global__ void energy_kernel(const PdArgs A, double eps, double delta, double C
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int x = i % A.W, y = i / A.W;
         const float* u = A.u;
-        acc += (double)A.alpha * (double)interp(A.cost + (size_t)i * A.L, A.L, u[i]);
+        acc += (double)alpha_at(A, i) * (double)interp(A, i, u[i]);
         if (x + 1 < A.W)
             acc += (double)A.lambda_r * A.wh[i] * r_dc((double)u[i] - (double)u[i + 1], eps, delta, C);
         if (y + 1 < A.H)
@@ -195,10 +222,8 @@ cudaError_t launch_linearise(const PdArgs& a, cudaStream_t s)
 
 cudaError_t launch_pd_iter(const PdArgs& a, cudaStream_t s)
 {
-    dim3 blk(32, 8);
-    dim3 grd((a.W + 31) / 32, (a.H + 7) / 8);
-    pd_u_kernel<<<grd, blk, 0, s>>>(a);
-    pd_pq_kernel<<<grd, blk, 0, s>>>(a);
+    dim3 grd((a.W + kTX - 1) / kTX, (a.H + kTY - 1) / kTY);
+    pd_fused_kernel<<<grd, kTX * kTY, 0, s>>>(a);
     return cudaGetLastError();
 }
 
