@@ -616,3 +616,266 @@ void or_convex_gap(int H, int W, int L, const double* cost, const double* alpha,
     *primal = pr;
     *dual = du;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reverse mode of the refinement (the differentiable form): gradient of the */
+/* loss mean_i |u_i - gt_i| of the refined disparity with respect to the     */
+/* cost samples, the per-pixel data weights alpha_i and lambda_r.  The       */
+/* labels that start the refinement are constants.  Every map of an          */
+/* iteration is piecewise linear; derivatives follow the branch the forward   */
+/* comparisons take (strict inequalities select the non-identity branch).    */
+/* ------------------------------------------------------------------------ */
+
+/* d interp(c, x) / dx with the argument clamp (1 inside [0, L-1], else 0) */
+static double interp_dx(int L, const double* c, double u)
+{
+    if (u < 0.0 || u > (double)(L - 1)) return 0.0;
+    double fl = floor(u);
+    int k = (int)fl;
+    if (k > L - 2) k = L - 2;
+    return c[k + 1] - c[k];
+}
+
+/* scatter w * d interp(c, x) / dc into g */
+static void interp_dc(int L, double u, double w, double* g)
+{
+    if (u < 0.0) u = 0.0;
+    if (u > (double)(L - 1)) u = (double)(L - 1);
+    double fl = floor(u);
+    int k = (int)fl;
+    if (k > L - 2) k = L - 2;
+    if (k < 0) k = 0;
+    double t = u - (double)k;
+    g[k] += w * (1.0 - t);
+    g[k + 1] += w * t;
+}
+
+/* forward of one prox of step * (omega r_{a,b})* with its derivatives */
+static double prox_conj_d(double t, double omega, double a, double b, double step, double* dt,
+                          double* domega)
+{
+    double tp, dtp = 1.0, dom = 0.0;
+    if (fabs(t) <= a * omega) {
+        tp = t;
+    } else {
+        double m = fabs(t) - b * step;
+        double s = t > 0 ? 1.0 : -1.0;
+        if (m > a * omega) { tp = s * m; dtp = 1.0; dom = 0.0; }
+        else { tp = s * a * omega; dtp = 0.0; dom = s * a; }
+    }
+    if (tp > omega) { tp = omega; dtp = 0.0; dom = 1.0; }
+    else if (tp < -omega) { tp = -omega; dtp = 0.0; dom = -1.0; }
+    *dt = dtp;
+    *domega = dom;
+    return tp;
+}
+
+int or_refine_grad(int H, int W, int L, const double* cost, const double* alpha, const double* wh,
+                   const double* wv, const double* uinit, int iters, const or_cont_params* P,
+                   const double* gt, double* u_out, double* loss, double* g_cost, double* g_alpha,
+                   double* g_lambda)
+{
+    if (H <= 0 || W <= 0 || L < 2 || P->warps <= 0 || iters < 0) return OR_ERR_ARG;
+    i64 N = (i64)H * W;
+    int T = iters;
+    /* per-iteration input states and per-warp linearisations */
+    double* U = (double*)malloc((size_t)(T + 1) * N * sizeof(double));
+    double* PH = (double*)malloc((size_t)(T + 1) * N * sizeof(double));
+    double* PV = (double*)malloc((size_t)(T + 1) * N * sizeof(double));
+    double* QH = (double*)malloc((size_t)(T + 1) * N * sizeof(double));
+    double* QV = (double*)malloc((size_t)(T + 1) * N * sizeof(double));
+    int nw = P->warps;
+    double* U0 = (double*)malloc((size_t)nw * N * sizeof(double));
+    double* S1 = (double*)malloc((size_t)nw * N * sizeof(double));
+    double* S2 = (double*)malloc((size_t)nw * N * sizeof(double));
+    double* LO = (double*)malloc((size_t)nw * N * sizeof(double));
+    double* HI = (double*)malloc((size_t)nw * N * sizeof(double));
+    int* wstart = (int*)malloc((size_t)(nw + 1) * sizeof(int));
+    const double bp = P->delta, ap = P->eps, bq = P->C + P->delta - P->eps * P->delta;
+    const double tau = P->tau, sigma = P->sigma, h = P->h;
+    for (i64 p = 0; p < N; ++p) { U[p] = uinit[p]; PH[p] = PV[p] = QH[p] = QV[p] = 0.0; }
+    int base = T / nw, extra = T % nw, it = 0;
+    for (int w = 0; w < nw; ++w) {
+        wstart[w] = it;
+        int nit = base + (w < extra ? 1 : 0);
+        for (i64 p = 0; p < N; ++p)
+            or_linearise_px(L, cost + p * L, alpha[p], U[(i64)it * N + p], h, &S1[w * N + p],
+                            &S2[w * N + p], &LO[w * N + p], &HI[w * N + p]);
+        for (i64 p = 0; p < N; ++p) U0[w * N + p] = U[(i64)it * N + p];
+        for (int k = 0; k < nit; ++k, ++it) {
+            const double *u = U + (i64)it * N, *ph = PH + (i64)it * N, *pv = PV + (i64)it * N;
+            const double *qh = QH + (i64)it * N, *qv = QV + (i64)it * N;
+            double *un = U + (i64)(it + 1) * N, *phn = PH + (i64)(it + 1) * N;
+            double *pvn = PV + (i64)(it + 1) * N, *qhn = QH + (i64)(it + 1) * N;
+            double *qvn = QV + (i64)(it + 1) * N;
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    i64 p = (i64)y * W + x;
+                    double div = 0.0;
+                    if (x + 1 < W) div += ph[p] - qh[p];
+                    if (x > 0) div -= ph[p - 1] - qh[p - 1];
+                    if (y + 1 < H) div += pv[p] - qv[p];
+                    if (y > 0) div -= pv[p - W] - qv[p - W];
+                    un[p] = or_prox_data(u[p] - tau * div, U0[w * N + p], S1[w * N + p], S2[w * N + p],
+                                         LO[w * N + p], HI[w * N + p], tau);
+                }
+            for (i64 p = 0; p < N; ++p) phn[p] = pvn[p] = qhn[p] = qvn[p] = 0.0;
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    i64 p = (i64)y * W + x;
+                    double d1, d2;
+                    if (x + 1 < W) {
+                        double om = P->lambda_r * wh[p];
+                        qhn[p] = prox_conj_d(qh[p] + tau * (u[p] - u[p + 1]), om, 0.0, bq, tau, &d1, &d2);
+                        phn[p] = prox_conj_d(ph[p] + sigma * ((2 * un[p] - u[p]) - (2 * un[p + 1] - u[p + 1])),
+                                             om, ap, bp, sigma, &d1, &d2);
+                    }
+                    if (y + 1 < H) {
+                        double om = P->lambda_r * wv[p];
+                        qvn[p] = prox_conj_d(qv[p] + tau * (u[p] - u[p + W]), om, 0.0, bq, tau, &d1, &d2);
+                        pvn[p] = prox_conj_d(pv[p] + sigma * ((2 * un[p] - u[p]) - (2 * un[p + W] - u[p + W])),
+                                             om, ap, bp, sigma, &d1, &d2);
+                    }
+                }
+        }
+    }
+    wstart[nw] = T;
+    /* loss and its adjoint */
+    const double* uT = U + (i64)T * N;
+    double Ls = 0.0;
+    double* ub = (double*)calloc((size_t)N, sizeof(double));   /* adjoint of u */
+    double* phb = (double*)calloc((size_t)N, sizeof(double));
+    double* pvb = (double*)calloc((size_t)N, sizeof(double));
+    double* qhb = (double*)calloc((size_t)N, sizeof(double));
+    double* qvb = (double*)calloc((size_t)N, sizeof(double));
+    for (i64 p = 0; p < N; ++p) {
+        double d = uT[p] - gt[p];
+        Ls += fabs(d);
+        ub[p] = (d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0)) / (double)N;
+        u_out[p] = uT[p];
+    }
+    *loss = Ls / (double)N;
+    for (i64 e = 0; e < N * L; ++e) g_cost[e] = 0.0;
+    for (i64 p = 0; p < N; ++p) g_alpha[p] = 0.0;
+    double glam = 0.0;
+    double* tqh = (double*)calloc((size_t)N, sizeof(double));
+    double* tqv = (double*)calloc((size_t)N, sizeof(double));
+    double* tph = (double*)calloc((size_t)N, sizeof(double));
+    double* tpv = (double*)calloc((size_t)N, sizeof(double));
+    double* uhb = (double*)calloc((size_t)N, sizeof(double));
+    double* nub = (double*)calloc((size_t)N, sizeof(double));
+    double* s1b = (double*)calloc((size_t)N, sizeof(double));
+    double* s2b = (double*)calloc((size_t)N, sizeof(double));
+    double* u0b = (double*)calloc((size_t)N, sizeof(double));
+    double* lob = (double*)calloc((size_t)N, sizeof(double));
+    double* hib = (double*)calloc((size_t)N, sizeof(double));
+    for (int w = nw - 1; w >= 0; --w) {
+        for (int k = wstart[w + 1] - 1; k >= wstart[w]; --k) {
+            const double *u = U + (i64)k * N, *un = U + (i64)(k + 1) * N;
+            const double *ph = PH + (i64)k * N, *pv = PV + (i64)k * N;
+            const double *qh = QH + (i64)k * N, *qv = QV + (i64)k * N;
+            /* adjoints of this iteration's outputs: ub (u+), phb.. (p+, q+) */
+            for (i64 p = 0; p < N; ++p) { tqh[p] = tqv[p] = tph[p] = tpv[p] = 0.0; }
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    i64 p = (i64)y * W + x;
+                    double dt, dom;
+                    if (x + 1 < W) {
+                        double om = P->lambda_r * wh[p];
+                        prox_conj_d(qh[p] + tau * (u[p] - u[p + 1]), om, 0.0, bq, tau, &dt, &dom);
+                        tqh[p] = qhb[p] * dt;
+                        glam += qhb[p] * dom * wh[p];
+                        prox_conj_d(ph[p] + sigma * ((2 * un[p] - u[p]) - (2 * un[p + 1] - u[p + 1])), om,
+                                    ap, bp, sigma, &dt, &dom);
+                        tph[p] = phb[p] * dt;
+                        glam += phb[p] * dom * wh[p];
+                    }
+                    if (y + 1 < H) {
+                        double om = P->lambda_r * wv[p];
+                        prox_conj_d(qv[p] + tau * (u[p] - u[p + W]), om, 0.0, bq, tau, &dt, &dom);
+                        tqv[p] = qvb[p] * dt;
+                        glam += qvb[p] * dom * wv[p];
+                        prox_conj_d(pv[p] + sigma * ((2 * un[p] - u[p]) - (2 * un[p + W] - u[p + W])), om,
+                                    ap, bp, sigma, &dt, &dom);
+                        tpv[p] = pvb[p] * dt;
+                        glam += pvb[p] * dom * wv[p];
+                    }
+                }
+            /* A^T of the edge adjoints per pixel; adjoint of u+ and of u_hat */
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    i64 p = (i64)y * W + x;
+                    double atp = 0.0, atq = 0.0;
+                    if (x + 1 < W) { atp += tph[p]; atq += tqh[p]; }
+                    if (x > 0) { atp -= tph[p - 1]; atq -= tqh[p - 1]; }
+                    if (y + 1 < H) { atp += tpv[p]; atq += tqv[p]; }
+                    if (y > 0) { atp -= tpv[p - W]; atq -= tqv[p - W]; }
+                    double wbar = sigma * atp;
+                    double unb = ub[p] + 2.0 * wbar;       /* total adjoint of u+ */
+                    nub[p] = -wbar + tau * atq;            /* direct paths into u */
+                    /* reverse of the data prox and the box clamp */
+                    double div = 0.0;
+                    if (x + 1 < W) div += ph[p] - qh[p];
+                    if (x > 0) div -= ph[p - 1] - qh[p - 1];
+                    if (y + 1 < H) div += pv[p] - qv[p];
+                    if (y > 0) div -= pv[p - W] - qv[p - W];
+                    double uh = u[p] - tau * div;
+                    double u0 = U0[w * N + p], ts1 = tau * S1[w * N + p], ts2 = tau * S2[w * N + p];
+                    int cs = uh > u0 + ts2 ? 0 : (uh < u0 + ts1 ? 1 : 2);
+                    double v = cs == 0 ? uh - ts2 : (cs == 1 ? uh - ts1 : u0);
+                    double lo = LO[w * N + p], hi = HI[w * N + p];
+                    if (v < lo) { lob[p] += unb; uhb[p] = 0.0; }
+                    else if (v > hi) { hib[p] += unb; uhb[p] = 0.0; }
+                    else if (cs == 0) { uhb[p] = unb; s2b[p] -= tau * unb; }
+                    else if (cs == 1) { uhb[p] = unb; s1b[p] -= tau * unb; }
+                    else { uhb[p] = 0.0; u0b[p] += unb; }
+                }
+            /* u_hat = u - tau A^T (p - q): adjoints of the inputs */
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    i64 p = (i64)y * W + x;
+                    ub[p] = nub[p] + uhb[p];
+                }
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    i64 p = (i64)y * W + x;
+                    if (x + 1 < W) {
+                        double d = uhb[p] - uhb[p + 1];
+                        phb[p] = tph[p] - tau * d;
+                        qhb[p] = tqh[p] + tau * d;
+                    }
+                    if (y + 1 < H) {
+                        double d = uhb[p] - uhb[p + W];
+                        pvb[p] = tpv[p] - tau * d;
+                        qvb[p] = tqv[p] + tau * d;
+                    }
+                }
+        }
+        /* reverse of the linearisation at the start of warp w */
+        for (i64 p = 0; p < N; ++p) {
+            const double* c = cost + p * L;
+            double u0 = U0[w * N + p], a = alpha[p];
+            double d0 = or_interp(L, c, u0), dm = or_interp(L, c, u0 - h), dp = or_interp(L, c, u0 + h);
+            double s1r = a * (d0 - dm) / h, s2r = a * (dp - d0) / h;
+            double b1 = s1b[p], b2 = s2b[p];
+            if (s2r < s1r) { double m = 0.5 * (b1 + b2); b1 = m; b2 = m; }
+            g_alpha[p] += b1 * (d0 - dm) / h + b2 * (dp - d0) / h;
+            double* gc = g_cost + p * L;
+            interp_dc(L, u0, a / h * (b1 - b2), gc);
+            interp_dc(L, u0 - h, -a / h * b1, gc);
+            interp_dc(L, u0 + h, a / h * b2, gc);
+            double gu = u0b[p];
+            gu += b1 * a / h * (interp_dx(L, c, u0) - interp_dx(L, c, u0 - h));
+            gu += b2 * a / h * (interp_dx(L, c, u0 + h) - interp_dx(L, c, u0));
+            if (u0 - h > 0.0) gu += lob[p];
+            if (u0 + h < (double)(L - 1)) gu += hib[p];
+            ub[p] += gu;
+            s1b[p] = s2b[p] = u0b[p] = lob[p] = hib[p] = 0.0;
+        }
+    }
+    *g_lambda = glam;
+    free(U); free(PH); free(PV); free(QH); free(QV); free(U0); free(S1); free(S2); free(LO); free(HI);
+    free(wstart); free(ub); free(phb); free(pvb); free(qhb); free(qvb); free(tqh); free(tqv);
+    free(tph); free(tpv); free(uhb); free(nub); free(s1b); free(s2b); free(u0b); free(lob); free(hib);
+    return OR_OK;
+}

@@ -90,6 +90,8 @@ def lib():
                                 ctypes.POINTER(ContParams)] + [f64p] * 5 + [ctypes.c_int, f64p])
         L.or_convex_gap.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4
                                     + [ctypes.POINTER(ContParams)] + [f64p] * 4 + [f64p, f64p])
+        L.or_refine_grad.argtypes = ([ctypes.c_int] * 3 + [f64p] * 5 + [ctypes.c_int,
+                                     ctypes.POINTER(ContParams)] + [f64p] * 6)
     return _lib
 
 
@@ -315,6 +317,28 @@ def convex_gap(cost, wh, wv, u0, u, ph, pv, P: Params, alpha=None):
                         _p(np.ascontiguousarray(pv, np.float64), f64p),
                         ctypes.byref(pr), ctypes.byref(du))
     return pr.value, du.value
+
+
+def refine_grad(cost, wh, wv, u0, iters: int, gt, P: Params = Params(), alpha=None):
+    """Reverse mode of the refinement: loss = mean |u - gt| and its gradient with
+    respect to the cost samples, the per-pixel data weights and lambda_r."""
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    H, W, L = cost.shape
+    al = np.ascontiguousarray(np.broadcast_to(P.alpha if alpha is None else alpha, (H, W)), np.float64)
+    u0 = np.ascontiguousarray(u0, dtype=np.float64).reshape(H, W)
+    gt = np.ascontiguousarray(gt, dtype=np.float64).reshape(H, W)
+    u = np.zeros((H, W))
+    loss = np.zeros(1)
+    gc = np.zeros((H, W, L))
+    ga = np.zeros((H, W))
+    gl = np.zeros(1)
+    cp = P.cont()
+    _chk(lib().or_refine_grad(H, W, L, _p(cost, f64p), _p(al, f64p),
+                              _p(np.ascontiguousarray(wh, np.float64), f64p),
+                              _p(np.ascontiguousarray(wv, np.float64), f64p), _p(u0, f64p), iters,
+                              ctypes.byref(cp), _p(gt, f64p), _p(u, f64p), _p(loss, f64p),
+                              _p(gc, f64p), _p(ga, f64p), _p(gl, f64p)), "refine_grad")
+    return u, float(loss[0]), gc, ga, float(gl[0])
 
 
 def solve(left, right, L: int, dmm_iters: int, pd_iters: int, P: Params = Params(),

@@ -186,3 +186,87 @@ def test_pins_catch_planted_mistakes(tmp_path, name, old, new):
                   *[p(s) for s in st], 1, p(en))
     pr, du = O.convex_gap(cost, wh, wv, u0, u, st[0], st[1], P)
     assert not (np.isfinite(pr) and abs(pr - du) <= 1e-9 * abs(pr)), f"not caught: {name}"
+
+
+# --- reverse mode of the refinement (the differentiable form) -----------------
+
+def _adjoint_problem(seed=2):
+    H, W, L = 12, 16, 16
+    sp = S.make_pair(H, W, L, planes=3, seed=seed)
+    rng = np.random.default_rng(seed)
+    cost = O.cost_volume(sp.left, sp.right, L).astype(float) + rng.uniform(0, 1, (H, W, L))
+    wh, wv = O.edge_weights(sp.left)
+    u0 = np.argmin(cost, -1).astype(float)
+    alpha = rng.uniform(0.5, 1.5, (H, W))
+    return cost, wh.astype(float), wv.astype(float), u0, alpha, sp.gt
+
+
+def _fd_directions(gradfn, lossfn, cost, alpha, lam, n, seed, h=1e-6):
+    """(finite difference, adjoint) pairs on random joint directions; a direction
+    whose difference quotients at h and h/2 disagree straddles a kink and is skipped."""
+    gc, ga, gl = gradfn
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        vc, va, vl = rng.normal(size=cost.shape), rng.normal(size=alpha.shape), rng.normal()
+        def q(hh):
+            return (lossfn(cost + hh * vc, alpha + hh * va, lam + hh * vl)
+                    - lossfn(cost - hh * vc, alpha - hh * va, lam - hh * vl)) / (2 * hh)
+        f1, f2 = q(h), q(h / 2)
+        if abs(f1 - f2) > 1e-6 * max(1.0, abs(f1)):
+            continue
+        out.append((f1, float((gc * vc).sum() + (ga * va).sum() + gl * vl)))
+    return out
+
+
+def test_refine_gradient_matches_finite_differences():
+    cost, wh, wv, u0, alpha, gt = _adjoint_problem()
+    iters, lam = 30, 1.2
+    P = O.Params(warps=3, lambda_r=lam)
+    u, loss, gc, ga, gl = O.refine_grad(cost, wh, wv, u0, iters, gt, P, alpha)
+    ur, _, _ = O.refine(cost, wh, wv, u0, iters, P, alpha)
+    assert np.array_equal(u, ur) and loss == pytest.approx(np.abs(ur - gt).mean(), rel=1e-15)
+
+    def lossfn(c, a, l):
+        uu, _, _ = O.refine(c, wh, wv, u0, iters, O.Params(warps=3, lambda_r=l), a)
+        return np.abs(uu - gt).mean()
+    pairs = _fd_directions((gc, ga, gl), lossfn, cost, alpha, lam, 16, seed=3)
+    assert len(pairs) >= 12
+    for fd, an in pairs:
+        assert an == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+ADJ_MUTATIONS = [
+    ("extrapolation factor dropped", "double unb = ub[p] + 2.0 * wbar;", "double unb = ub[p] + wbar;"),
+    ("data slope sign", "s2b[p] -= tau * unb;", "s2b[p] += tau * unb;"),
+    ("convexity fix not reversed", "if (s2r < s1r) { double m = 0.5 * (b1 + b2); b1 = m; b2 = m; }", "(void)0;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", ADJ_MUTATIONS)
+def test_adjoint_pin_catches_planted_mistakes(tmp_path, name, old, new):
+    src = open(os.path.join(os.path.dirname(O.__file__), "dm_oracle.c")).read()
+    assert old in src, name
+    mut = tmp_path / "mut.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(mut), "-lm"],
+                   check=True)
+    lib = ctypes.CDLL(str(so))
+    f64p = ctypes.POINTER(ctypes.c_double)
+    lib.or_refine_grad.argtypes = ([ctypes.c_int] * 3 + [f64p] * 5 + [ctypes.c_int,
+                                   ctypes.POINTER(O.ContParams)] + [f64p] * 6)
+    cost, wh, wv, u0, alpha, gt = _adjoint_problem()
+    H, W, L = cost.shape
+    iters, lam = 30, 1.2
+    cp = O.Params(warps=3, lambda_r=lam).cont()
+    u, loss, gc, ga, gl = np.zeros((H, W)), np.zeros(1), np.zeros((H, W, L)), np.zeros((H, W)), np.zeros(1)
+    p = lambda a: np.ascontiguousarray(a).ctypes.data_as(f64p)
+    lib.or_refine_grad(H, W, L, p(cost), p(alpha), p(wh), p(wv), p(u0), iters, ctypes.byref(cp),
+                       p(gt), p(u), p(loss), p(gc), p(ga), p(gl))
+
+    def lossfn(c, a, l):
+        uu, _, _ = O.refine(c, wh, wv, u0, iters, O.Params(warps=3, lambda_r=l), a)
+        return np.abs(uu - gt).mean()
+    pairs = _fd_directions((gc, ga, float(gl[0])), lossfn, cost, alpha, lam, 16, seed=3)
+    assert any(abs(an - fd) > 1e-6 * max(abs(fd), 1e-3) for fd, an in pairs), f"not caught: {name}"
