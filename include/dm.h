@@ -170,6 +170,76 @@ DM_API int dm_get_lower_bounds(dm_ctx* ctx, int64_t* h_lb, int n);
  * (Eq. mrf_formulation) of the current disparity; synchronous. */
 DM_API int dm_energy(dm_ctx* ctx, double* h_energy);
 
+/* ---- Differentiable refinement -------------------------------------------
+ * The refinement of dm_refine is a fixed sequence of primal-dual iterations
+ * (Eq. cont_iterates) with a re-linearised data term (Sec. 3.1); these calls
+ * give it on a float32 cost volume and its reverse mode: gradients of a loss
+ * of the refined disparity with respect to the cost volume, the per-pixel
+ * data weights alpha and the regularisation weight lambda_r.  The paper runs
+ * the iteration forward only; the reverse follows the chain rule through the
+ * same iterates, with every piecewise-linear prox differentiated on the branch
+ * the forward took (at a tie, the branch whose slope in its argument is 0).
+ */
+
+/* Continuous stage on a caller's float32 cost volume d_cost [H][W][L]
+ * (device, 4-byte aligned).  The context BORROWS d_cost: it must stay valid
+ * and unchanged until the next dm_set_cost_volume*, dm_cost_volume or
+ * dm_destroy.  d_wh, d_wv ([H][W] uint8 edge weights) are copied; both NULL
+ * keeps the weights of an earlier dm_cost_volume / dm_set_cost_volume
+ * (DM_ERR_STATE if there are none).  While a float cost volume is set the
+ * discrete stage returns DM_ERR_STATE (its arithmetic is integer); dm_refine,
+ * dm_energy and the calls below use the float samples.  Labels of an earlier
+ * dm_discrete stay available as a starting point. */
+DM_API int dm_set_cost_volume_f32(dm_ctx* ctx, const float* d_cost, const uint8_t* d_wh,
+                                  const uint8_t* d_wv);
+
+/* Per-pixel data-term weights alpha_i (d_alpha: [H][W] float32, device,
+ * borrowed like d_cost above) in place of the scalar params.alpha; NULL
+ * returns to the scalar.  Applies to dm_refine, dm_energy and the calls
+ * below. */
+DM_API int dm_set_data_weights(dm_ctx* ctx, const float* d_alpha);
+
+/* Regularisation weight lambda_r of the continuous stage (>= 0, finite). */
+DM_API int dm_set_lambda_r(dm_ctx* ctx, double lambda_r);
+
+/* Bytes of device tape that dm_refine_tape needs for iters iterations with a
+ * checkpoint every ckpt_every iterations (>= 1).  The tape holds the state
+ * (u, p, q: five H x W float32 arrays) at every checkpoint and at every warp
+ * start, room to recompute one segment, and the reverse pass's scratch. */
+DM_API int dm_tape_bytes(const dm_ctx* ctx, int iters, int ckpt_every, size_t* bytes);
+
+/* dm_refine with checkpoints: the same iterations and result (read with
+ * dm_get_disparity), and the states needed by dm_refine_backward written to
+ * d_tape (device, 256-byte aligned, >= dm_tape_bytes; DM_ERR_WORKSPACE
+ * otherwise).  d_u0 as in dm_refine. */
+DM_API int dm_refine_tape(dm_ctx* ctx, int iters, int ckpt_every, const float* d_u0, void* d_tape,
+                          size_t tape_bytes);
+
+/* Reverse mode of the last dm_refine_tape on this context (the same d_tape
+ * and tape_bytes; DM_ERR_STATE if the tape or any input changed since).
+ * d_gu: d loss / d u of the refined disparity ([H][W] float32).  Outputs,
+ * each nullable and overwritten: d_gcost [H][W][L] float32 (d loss / d cost),
+ * d_galpha [H][W] float32 (d loss / d alpha_i; with a scalar alpha the
+ * derivative in it is the sum), d_glambda one float64 (d loss / d lambda_r),
+ * d_gu0 [H][W] float32 (d loss / d u0).  Each segment between checkpoints is
+ * recomputed from its checkpoint, then reversed one iteration per kernel.  The
+ * tape stays valid: the call may be repeated with another d_gu. */
+DM_API int dm_refine_backward(dm_ctx* ctx, const float* d_gu, void* d_tape, size_t tape_bytes,
+                              float* d_gcost, float* d_galpha, double* d_glambda, float* d_gu0);
+
+/* Forward mode of the same refinement: runs dm_refine(iters, d_u0) (result
+ * readable with dm_get_disparity) and writes to d_du ([H][W] float32) the
+ * directional derivative of the refined disparity in the direction
+ * (d_du0, d_dcost, d_dalpha, dlambda) of (u0, the float cost volume, alpha,
+ * lambda_r); NULL directions are zero.  Derivatives are taken on the branches
+ * the forward takes, as in dm_refine_backward, so for any direction v and
+ * any d_gu the pair satisfies <d_gu, J v> = <J^T d_gu, v>.  d_scratch:
+ * device, 256-byte aligned, >= dm_jvp_bytes (15 H x W float32 arrays). */
+DM_API int dm_jvp_bytes(const dm_ctx* ctx, size_t* bytes);
+DM_API int dm_refine_jvp(dm_ctx* ctx, int iters, const float* d_u0, const float* d_du0,
+                         const float* d_dcost, const float* d_dalpha, double dlambda, float* d_du,
+                         void* d_scratch, size_t scratch_bytes);
+
 /* Allocation-free variant of dm_discrete_pass.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
  * (a fixed memory budget decided at start-up, a real-time or embedded

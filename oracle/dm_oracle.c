@@ -655,11 +655,11 @@ static double prox_conj_d(double t, double omega, double a, double b, double ste
                           double* domega)
 {
     double tp, dtp = 1.0, dom = 0.0;
-    if (fabs(t) <= a * omega) {
+    if (fabs(t) < a * omega) {
         tp = t;
     } else {
         double m = fabs(t) - b * step;
-        double s = t > 0 ? 1.0 : -1.0;
+        double s = t > 0 ? 1.0 : (t < 0 ? -1.0 : 0.0);
         if (m > a * omega) { tp = s * m; dtp = 1.0; dom = 0.0; }
         else { tp = s * a * omega; dtp = 0.0; dom = s * a; }
     }
@@ -673,7 +673,7 @@ static double prox_conj_d(double t, double omega, double a, double b, double ste
 int or_refine_grad(int H, int W, int L, const double* cost, const double* alpha, const double* wh,
                    const double* wv, const double* uinit, int iters, const or_cont_params* P,
                    const double* gt, double* u_out, double* loss, double* g_cost, double* g_alpha,
-                   double* g_lambda)
+                   double* g_lambda, double* g_u0)
 {
     if (H <= 0 || W <= 0 || L < 2 || P->warps <= 0 || iters < 0) return OR_ERR_ARG;
     i64 N = (i64)H * W;
@@ -874,6 +874,8 @@ int or_refine_grad(int H, int W, int L, const double* cost, const double* alpha,
         }
     }
     *g_lambda = glam;
+    if (g_u0 != NULL)
+        for (i64 p = 0; p < N; ++p) g_u0[p] = ub[p];
     free(U); free(PH); free(PV); free(QH); free(QV); free(U0); free(S1); free(S2); free(LO); free(HI);
     free(wstart); free(ub); free(phb); free(pvb); free(qhb); free(qvb); free(tqh); free(tqv);
     free(tph); free(tpv); free(uhb); free(nub); free(s1b); free(s2b); free(u0b); free(lob); free(hib);

@@ -91,7 +91,7 @@ def lib():
         L.or_convex_gap.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4
                                     + [ctypes.POINTER(ContParams)] + [f64p] * 4 + [f64p, f64p])
         L.or_refine_grad.argtypes = ([ctypes.c_int] * 3 + [f64p] * 5 + [ctypes.c_int,
-                                     ctypes.POINTER(ContParams)] + [f64p] * 6)
+                                     ctypes.POINTER(ContParams)] + [f64p] * 7)
     return _lib
 
 
@@ -319,9 +319,11 @@ def convex_gap(cost, wh, wv, u0, u, ph, pv, P: Params, alpha=None):
     return pr.value, du.value
 
 
-def refine_grad(cost, wh, wv, u0, iters: int, gt, P: Params = Params(), alpha=None):
+def refine_grad(cost, wh, wv, u0, iters: int, gt, P: Params = Params(), alpha=None,
+                want_u0: bool = False):
     """Reverse mode of the refinement: loss = mean |u - gt| and its gradient with
-    respect to the cost samples, the per-pixel data weights and lambda_r."""
+    respect to the cost samples, the per-pixel data weights and lambda_r (and,
+    with want_u0, the start u0: a sixth result)."""
     cost = np.ascontiguousarray(cost, dtype=np.float64)
     H, W, L = cost.shape
     al = np.ascontiguousarray(np.broadcast_to(P.alpha if alpha is None else alpha, (H, W)), np.float64)
@@ -332,12 +334,16 @@ def refine_grad(cost, wh, wv, u0, iters: int, gt, P: Params = Params(), alpha=No
     gc = np.zeros((H, W, L))
     ga = np.zeros((H, W))
     gl = np.zeros(1)
+    g0 = np.zeros((H, W))
     cp = P.cont()
     _chk(lib().or_refine_grad(H, W, L, _p(cost, f64p), _p(al, f64p),
                               _p(np.ascontiguousarray(wh, np.float64), f64p),
                               _p(np.ascontiguousarray(wv, np.float64), f64p), _p(u0, f64p), iters,
                               ctypes.byref(cp), _p(gt, f64p), _p(u, f64p), _p(loss, f64p),
-                              _p(gc, f64p), _p(ga, f64p), _p(gl, f64p)), "refine_grad")
+                              _p(gc, f64p), _p(ga, f64p), _p(gl, f64p), _p(g0, f64p)),
+         "refine_grad")
+    if want_u0:
+        return u, float(loss[0]), gc, ga, float(gl[0]), g0
     return u, float(loss[0]), gc, ga, float(gl[0])
 
 

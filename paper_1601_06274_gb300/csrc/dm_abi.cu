@@ -34,6 +34,15 @@ struct dm_ctx {
     int pq_cur = 0;             // 0: current p, q in lay.ph.., 1: in lay.ph2..
     int last_iters = 0;
     unsigned long long launches = 0;  // kernels enqueued by this context
+    bool have_weights = false;  // edge weights in the workspace
+    // differentiable form: a caller's float cost volume and per-pixel data
+    // weights (borrowed, nullable) and the tape of the last checkpointed forward
+    const float* cost_f32 = nullptr;
+    const float* alpha_px = nullptr;
+    const void* tape = nullptr;
+    size_t tape_bytes = 0;
+    int tape_iters = 0, tape_ckpt = 0;
+    bool tape_valid = false;
 };
 
 namespace {
@@ -150,9 +159,109 @@ dm::PdArgs pd_args(dm_ctx* c)
     a.pv2 = out[1];
     a.qh2 = out[2];
     a.qv2 = out[3];
-    a.costf = nullptr;
-    a.alpha_px = nullptr;
+    a.costf = c->cost_f32;
+    a.alpha_px = c->alpha_px;
     return a;
+}
+
+// one primal-dual state (u, p_h, p_v, q_h, q_v)
+struct St {
+    float* u;
+    float* ph;
+    float* pv;
+    float* qh;
+    float* qv;
+};
+
+St state_at(uint8_t* base, size_t slot)
+{
+    return {reinterpret_cast<float*>(base), reinterpret_cast<float*>(base + slot),
+            reinterpret_cast<float*>(base + 2 * slot), reinterpret_cast<float*>(base + 3 * slot),
+            reinterpret_cast<float*>(base + 4 * slot)};
+}
+
+St ws_set(dm_ctx* c, int which)
+{
+    uint8_t* ws = c->ws;
+    const dm::Layout& l = c->lay;
+    auto f = [&](size_t off) { return reinterpret_cast<float*>(ws + off); };
+    if (which == 0) return {f(l.u), f(l.ph), f(l.pv), f(l.qh), f(l.qv)};
+    return {f(l.u_new), f(l.ph2), f(l.pv2), f(l.qh2), f(l.qv2)};
+}
+
+dm::PdArgs pd_args_st(dm_ctx* c, const St& in, const St& out)
+{
+    dm::PdArgs a = pd_args(c);
+    a.u = in.u;
+    a.ph = in.ph;
+    a.pv = in.pv;
+    a.qh = in.qh;
+    a.qv = in.qv;
+    a.u_new = out.u;
+    a.ph2 = out.ph;
+    a.pv2 = out.pv;
+    a.qh2 = out.qh;
+    a.qv2 = out.qv;
+    return a;
+}
+
+// Tape of the checkpointed forward: the state at every segment start (every
+// ckpt_every iterations and every warp start, so no segment crosses a
+// re-linearisation), slots to recompute one segment, two adjoint states, the
+// per-pixel accumulators and the partial sums of d loss / d lambda_r.
+struct TapePlan {
+    std::vector<int> seg;         // first iteration of each segment
+    std::vector<char> warp_first; // segment starts a warp
+    std::vector<int> warp_seg;    // segment holding the start of its warp
+    int iters = 0, max_len = 0;
+    size_t slot = 0, off_ckpt = 0, off_seg = 0, off_adj = 0, off_acc = 0, off_part = 0, total = 0;
+};
+
+constexpr int kMaxTapeIters = 1 << 20;
+
+int make_plan(const dm_ctx* c, int iters, int ckpt, TapePlan* tp)
+{
+    if (iters < 0 || iters > kMaxTapeIters || ckpt < 1) return DM_ERR_ARG;
+    const int warps = c->p.warps, base = iters / warps, extra = iters % warps;
+    std::vector<char> wstart(iters + 1, 0);
+    for (int w = 0, k = 0; w < warps; ++w) {
+        const int nit = base + (w < extra ? 1 : 0);
+        if (nit > 0) wstart[k] = 1;
+        k += nit;
+    }
+    tp->iters = iters;
+    tp->seg.clear();
+    tp->warp_first.clear();
+    tp->warp_seg.clear();
+    int cur_warp_seg = 0;
+    for (int k = 0; k < iters; ++k) {
+        if (k % ckpt == 0 || wstart[k]) {
+            if (wstart[k]) cur_warp_seg = (int)tp->seg.size();
+            tp->seg.push_back(k);
+            tp->warp_first.push_back(wstart[k]);
+            tp->warp_seg.push_back(cur_warp_seg);
+        }
+    }
+    if (tp->seg.empty()) {  // no iterations: the tape holds the start state only
+        tp->seg.push_back(0);
+        tp->warp_first.push_back(0);
+        tp->warp_seg.push_back(0);
+    }
+    tp->max_len = 0;
+    for (size_t s = 0; s < tp->seg.size(); ++s) {
+        const int end = s + 1 < tp->seg.size() ? tp->seg[s + 1] : iters;
+        if (end - tp->seg[s] > tp->max_len) tp->max_len = end - tp->seg[s];
+    }
+    const size_t HW = (size_t)c->H * c->W;
+    tp->slot = align_up(HW * sizeof(float), 256);
+    const size_t st = 5 * tp->slot;
+    tp->off_ckpt = 0;
+    tp->off_seg = tp->off_ckpt + tp->seg.size() * st;
+    tp->off_adj = tp->off_seg + (size_t)tp->max_len * st;
+    tp->off_acc = tp->off_adj + 2 * st;
+    tp->off_part = tp->off_acc + 4 * tp->slot;
+    tp->total = tp->off_part + align_up(1024 * sizeof(double), 256);
+    return DM_OK;
 }
 
 int check_device_error(dm_ctx* c)
@@ -400,7 +509,8 @@ DM_API int dm_bind_workspace(dm_ctx* ctx, void* d_workspace, size_t bytes)
         return DM_ERR_WORKSPACE;
     ctx->ws = static_cast<uint8_t*>(d_workspace);
     ctx->ws_bytes = bytes;
-    ctx->have_cost = ctx->have_labels = ctx->have_u = false;
+    ctx->have_cost = ctx->have_labels = ctx->have_u = ctx->have_weights = false;
+    ctx->tape_valid = false;
     ctx->u_cur = 0;
     ctx->last_iters = 0;
     DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.taps, ctx->taps.data(),
@@ -454,6 +564,9 @@ DM_API int dm_cost_volume(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_r
                           ctx->stream));
     ctx->launches += 2;
     ctx->have_cost = true;
+    ctx->have_weights = true;
+    ctx->cost_f32 = nullptr;
+    ctx->tape_valid = false;
     if ((rc = choose_path(ctx, ctx->p.census_win * ctx->p.census_win - 1, false))) return rc;
     return dm_reset_duals(ctx);
 }
@@ -470,6 +583,9 @@ DM_API int dm_set_cost_volume(dm_ctx* ctx, const uint8_t* d_cost, const uint8_t*
     DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.wh, d_wh, HW, cudaMemcpyDeviceToDevice, ctx->stream));
     DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.wv, d_wv, HW, cudaMemcpyDeviceToDevice, ctx->stream));
     ctx->have_cost = true;
+    ctx->have_weights = true;
+    ctx->cost_f32 = nullptr;
+    ctx->tape_valid = false;
     if ((rc = choose_path(ctx, 255, true))) return rc;
     return dm_reset_duals(ctx);
 }
@@ -479,7 +595,7 @@ DM_API int dm_discrete_pass(dm_ctx* ctx, int which)
     if (ctx == nullptr || (which != 0 && which != 1) || !ctx->discrete_ok) return DM_ERR_ARG;
     int rc = ready(ctx);
     if (rc) return rc;
-    if (!ctx->have_cost) return DM_ERR_STATE;
+    if (!ctx->have_cost || ctx->cost_f32 != nullptr) return DM_ERR_STATE;
     return run_pass(ctx, which, nullptr, nullptr);
 }
 
@@ -488,7 +604,7 @@ DM_API int dm_discrete(dm_ctx* ctx, int iters, int64_t* h_lb)
     if (ctx == nullptr || iters < 1 || iters > kMaxIters || !ctx->discrete_ok) return DM_ERR_ARG;
     int rc = ready(ctx);
     if (rc) return rc;
-    if (!ctx->have_cost) return DM_ERR_STATE;
+    if (!ctx->have_cost || ctx->cost_f32 != nullptr) return DM_ERR_STATE;
     long long* lb = reinterpret_cast<long long*>(ctx->ws + ctx->lay.lb);
     uint16_t* labels = reinterpret_cast<uint16_t*>(ctx->ws + ctx->lay.labels);
     DM_CK(cudaMemsetAsync(lb, 0, iters * sizeof(long long), ctx->stream));
@@ -540,6 +656,330 @@ DM_API int dm_refine(dm_ctx* ctx, int iters, const float* d_u0)
             ctx->pq_cur ^= 1;
         }
     }
+    ctx->have_u = true;
+    return DM_OK;
+}
+
+DM_API int dm_set_cost_volume_f32(dm_ctx* ctx, const float* d_cost, const uint8_t* d_wh,
+                                  const uint8_t* d_wv)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (d_cost == nullptr || (d_wh == nullptr) != (d_wv == nullptr)) return DM_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(d_cost) & 3) return DM_ERR_ARG;
+    if (d_wh != nullptr) {
+        const size_t HW = (size_t)ctx->H * ctx->W;
+        DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.wh, d_wh, HW, cudaMemcpyDeviceToDevice,
+                              ctx->stream));
+        DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.wv, d_wv, HW, cudaMemcpyDeviceToDevice,
+                              ctx->stream));
+        ctx->have_weights = true;
+    }
+    if (!ctx->have_weights) return DM_ERR_STATE;
+    ctx->cost_f32 = d_cost;
+    ctx->have_cost = true;
+    ctx->tape_valid = false;
+    return DM_OK;
+}
+
+DM_API int dm_set_data_weights(dm_ctx* ctx, const float* d_alpha)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (reinterpret_cast<uintptr_t>(d_alpha) & 3) return DM_ERR_ARG;
+    ctx->alpha_px = d_alpha;
+    ctx->tape_valid = false;
+    return DM_OK;
+}
+
+DM_API int dm_set_lambda_r(dm_ctx* ctx, double lambda_r)
+{
+    if (ctx == nullptr || !(lambda_r >= 0.0) || !std::isfinite(lambda_r)) return DM_ERR_ARG;
+    ctx->p.lambda_r = lambda_r;
+    ctx->tape_valid = false;
+    return DM_OK;
+}
+
+DM_API int dm_tape_bytes(const dm_ctx* ctx, int iters, int ckpt_every, size_t* bytes)
+{
+    if (ctx == nullptr || bytes == nullptr) return DM_ERR_ARG;
+    TapePlan tp;
+    int rc = make_plan(ctx, iters, ckpt_every, &tp);
+    if (rc) return rc;
+    *bytes = tp.total;
+    return DM_OK;
+}
+
+DM_API int dm_refine_tape(dm_ctx* ctx, int iters, int ckpt_every, const float* d_u0, void* d_tape,
+                          size_t tape_bytes)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    TapePlan tp;
+    if ((rc = make_plan(ctx, iters, ckpt_every, &tp))) return rc;
+    if (!ctx->have_cost) return DM_ERR_STATE;
+    if (d_u0 == nullptr && !ctx->have_labels) return DM_ERR_STATE;
+    if (d_tape == nullptr || tape_bytes < tp.total ||
+        (reinterpret_cast<uintptr_t>(d_tape) & 255) != 0)
+        return DM_ERR_WORKSPACE;
+    ctx->tape_valid = false;
+    const int n = ctx->H * ctx->W;
+    uint8_t* T = static_cast<uint8_t*>(d_tape);
+    auto ckpt = [&](size_t s) { return state_at(T + tp.off_ckpt + s * 5 * tp.slot, tp.slot); };
+    St cur = ckpt(0);
+    if (d_u0 != nullptr)
+        DM_CK(cudaMemcpyAsync(cur.u, d_u0, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+    else {
+        DM_CK(dm::launch_init_u_from_labels(
+            reinterpret_cast<const uint16_t*>(ctx->ws + ctx->lay.labels), cur.u, n, ctx->stream));
+        ctx->launches += 1;
+    }
+    DM_CK(cudaMemsetAsync(cur.ph, 0, 4 * tp.slot, ctx->stream));
+    int curset = 2;  // 0, 1: workspace sets, 2: a checkpoint slot
+    size_t s_next = 1;
+    const int warps = ctx->p.warps, base = iters / warps, extra = iters % warps;
+    for (int w = 0, k = 0; w < warps; ++w) {
+        const int nit = base + (w < extra ? 1 : 0);
+        if (nit == 0) continue;
+        DM_CK(dm::launch_linearise(pd_args_st(ctx, cur, cur), ctx->stream));
+        ctx->launches += 1;
+        for (int it = 0; it < nit; ++it, ++k) {
+            St out;
+            int outset;
+            if (s_next < tp.seg.size() && tp.seg[s_next] == k + 1) {
+                out = ckpt(s_next++);
+                outset = 2;
+            } else {
+                outset = curset == 0 ? 1 : 0;
+                out = ws_set(ctx, outset);
+            }
+            DM_CK(dm::launch_pd_iter(pd_args_st(ctx, cur, out), ctx->stream));
+            ctx->launches += 1;
+            cur = out;
+            curset = outset;
+        }
+    }
+    if (curset == 2) {  // no iterations: the start state becomes the current one
+        const St a = ws_set(ctx, 0);
+        float* src[5] = {cur.u, cur.ph, cur.pv, cur.qh, cur.qv};
+        float* dst[5] = {a.u, a.ph, a.pv, a.qh, a.qv};
+        for (int j = 0; j < 5; ++j)
+            DM_CK(cudaMemcpyAsync(dst[j], src[j], n * sizeof(float), cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+        curset = 0;
+    }
+    ctx->u_cur = ctx->pq_cur = curset;
+    ctx->have_u = true;
+    ctx->tape = d_tape;
+    ctx->tape_bytes = tape_bytes;
+    ctx->tape_iters = iters;
+    ctx->tape_ckpt = ckpt_every;
+    ctx->tape_valid = true;
+    return DM_OK;
+}
+
+DM_API int dm_refine_backward(dm_ctx* ctx, const float* d_gu, void* d_tape, size_t tape_bytes,
+                              float* d_gcost, float* d_galpha, double* d_glambda, float* d_gu0)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (d_gu == nullptr) return DM_ERR_ARG;
+    if (!ctx->tape_valid || d_tape != ctx->tape || tape_bytes != ctx->tape_bytes)
+        return DM_ERR_STATE;
+    TapePlan tp;
+    if ((rc = make_plan(ctx, ctx->tape_iters, ctx->tape_ckpt, &tp))) return rc;
+    const int n = ctx->H * ctx->W;
+    const size_t HWL = (size_t)n * ctx->L;
+    uint8_t* T = static_cast<uint8_t*>(d_tape);
+    auto ckpt = [&](size_t s) { return state_at(T + tp.off_ckpt + s * 5 * tp.slot, tp.slot); };
+    auto segst = [&](int j) { return state_at(T + tp.off_seg + (size_t)j * 5 * tp.slot, tp.slot); };
+    St adj[2] = {state_at(T + tp.off_adj, tp.slot), state_at(T + tp.off_adj + 5 * tp.slot, tp.slot)};
+    float* acc = reinterpret_cast<float*>(T + tp.off_acc);
+    float* gu0 = acc;
+    float* gs1 = reinterpret_cast<float*>(T + tp.off_acc + tp.slot);
+    float* gs2 = reinterpret_cast<float*>(T + tp.off_acc + 2 * tp.slot);
+    float* glam = reinterpret_cast<float*>(T + tp.off_acc + 3 * tp.slot);
+    if (d_gcost != nullptr) DM_CK(cudaMemsetAsync(d_gcost, 0, HWL * sizeof(float), ctx->stream));
+    if (d_galpha != nullptr) DM_CK(cudaMemsetAsync(d_galpha, 0, n * sizeof(float), ctx->stream));
+    DM_CK(cudaMemsetAsync(acc, 0, 4 * tp.slot, ctx->stream));
+    DM_CK(cudaMemcpyAsync(adj[0].u, d_gu, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+    DM_CK(cudaMemsetAsync(adj[0].ph, 0, 4 * tp.slot, ctx->stream));
+    int cur = 0;
+    const dm::PdArgs P = pd_args(ctx);
+    for (int s = (int)tp.seg.size() - 1; s >= 0; --s) {
+        const int k0 = tp.seg[s];
+        const int k1 = s + 1 < (int)tp.seg.size() ? tp.seg[s + 1] : tp.iters;
+        const int len = k1 - k0;
+        if (len <= 0) continue;
+        const St wst = ckpt(tp.warp_seg[s]);
+        DM_CK(dm::launch_linearise(pd_args_st(ctx, wst, wst), ctx->stream));
+        ctx->launches += 1;
+        auto st = [&](int j) { return j == 0 ? ckpt(s) : segst(j - 1); };
+        for (int j = 0; j < len; ++j) {
+            DM_CK(dm::launch_pd_iter(pd_args_st(ctx, st(j), st(j + 1)), ctx->stream));
+            ctx->launches += 1;
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            const St in = st(j);
+            dm::AdjArgs a{};
+            a.H = ctx->H;
+            a.W = ctx->W;
+            a.L = ctx->L;
+            a.wh = P.wh;
+            a.wv = P.wv;
+            a.lambda_r = P.lambda_r;
+            a.tau = P.tau;
+            a.sigma = P.sigma;
+            a.h = P.h;
+            a.ap = P.ap;
+            a.bp = P.bp;
+            a.bq = P.bq;
+            a.u = in.u;
+            a.un = st(j + 1).u;
+            a.ph = in.ph;
+            a.pv = in.pv;
+            a.qh = in.qh;
+            a.qv = in.qv;
+            a.u0 = P.u0;
+            a.s1 = P.s1;
+            a.s2 = P.s2;
+            a.lo = P.lo;
+            a.hi = P.hi;
+            a.ub = adj[cur].u;
+            a.phb = adj[cur].ph;
+            a.pvb = adj[cur].pv;
+            a.qhb = adj[cur].qh;
+            a.qvb = adj[cur].qv;
+            a.ub2 = adj[cur ^ 1].u;
+            a.phb2 = adj[cur ^ 1].ph;
+            a.pvb2 = adj[cur ^ 1].pv;
+            a.qhb2 = adj[cur ^ 1].qh;
+            a.qvb2 = adj[cur ^ 1].qv;
+            a.gu0 = gu0;
+            a.gs1 = gs1;
+            a.gs2 = gs2;
+            a.glam = glam;
+            DM_CK(dm::launch_pd_adjoint(a, ctx->stream));
+            ctx->launches += 1;
+            cur ^= 1;
+        }
+        if (tp.warp_first[s]) {
+            dm::LinAdjArgs b{};
+            b.H = ctx->H;
+            b.W = ctx->W;
+            b.L = ctx->L;
+            b.cost = P.cost;
+            b.costf = P.costf;
+            b.alpha_px = P.alpha_px;
+            b.alpha = P.alpha;
+            b.h = P.h;
+            b.u0 = ckpt(s).u;
+            b.gu0 = gu0;
+            b.gs1 = gs1;
+            b.gs2 = gs2;
+            b.ub = adj[cur].u;
+            b.gcost = d_gcost;
+            b.galpha = d_galpha;
+            DM_CK(dm::launch_lin_adjoint(b, ctx->stream));
+            ctx->launches += 1;
+        }
+    }
+    if (d_glambda != nullptr) {
+        DM_CK(dm::launch_sum_f32(glam, n, reinterpret_cast<double*>(T + tp.off_part), d_glambda,
+                                 ctx->stream));
+        ctx->launches += 2;
+    }
+    if (d_gu0 != nullptr)
+        DM_CK(cudaMemcpyAsync(d_gu0, adj[cur].u, n * sizeof(float), cudaMemcpyDeviceToDevice,
+                              ctx->stream));
+    return DM_OK;
+}
+
+DM_API int dm_jvp_bytes(const dm_ctx* ctx, size_t* bytes)
+{
+    if (ctx == nullptr || bytes == nullptr) return DM_ERR_ARG;
+    *bytes = 15 * align_up((size_t)ctx->H * ctx->W * sizeof(float), 256);
+    return DM_OK;
+}
+
+DM_API int dm_refine_jvp(dm_ctx* ctx, int iters, const float* d_u0, const float* d_du0,
+                         const float* d_dcost, const float* d_dalpha, double dlambda, float* d_du,
+                         void* d_scratch, size_t scratch_bytes)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (iters < 0 || d_du == nullptr || !std::isfinite(dlambda)) return DM_ERR_ARG;
+    if (!ctx->have_cost) return DM_ERR_STATE;
+    if (d_u0 == nullptr && !ctx->have_labels) return DM_ERR_STATE;
+    size_t need;
+    dm_jvp_bytes(ctx, &need);
+    if (d_scratch == nullptr || scratch_bytes < need ||
+        (reinterpret_cast<uintptr_t>(d_scratch) & 255) != 0)
+        return DM_ERR_WORKSPACE;
+    const int n = ctx->H * ctx->W;
+    const size_t slot = align_up((size_t)n * sizeof(float), 256);
+    uint8_t* S = static_cast<uint8_t*>(d_scratch);
+    St tg[2] = {state_at(S, slot), state_at(S + 5 * slot, slot)};
+    St lin = state_at(S + 10 * slot, slot);  // du0, ds1, ds2, dlo, dhi
+    St cur = ws_set(ctx, 0);
+    if (d_u0 != nullptr)
+        DM_CK(cudaMemcpyAsync(cur.u, d_u0, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+    else {
+        DM_CK(dm::launch_init_u_from_labels(
+            reinterpret_cast<const uint16_t*>(ctx->ws + ctx->lay.labels), cur.u, n, ctx->stream));
+        ctx->launches += 1;
+    }
+    for (float* z : {cur.ph, cur.pv, cur.qh, cur.qv}) {
+        DM_CK(dm::launch_zero_f32(z, n, ctx->stream));
+        ctx->launches += 1;
+    }
+    if (d_du0 != nullptr)
+        DM_CK(cudaMemcpyAsync(tg[0].u, d_du0, n * sizeof(float), cudaMemcpyDeviceToDevice,
+                              ctx->stream));
+    else
+        DM_CK(cudaMemsetAsync(tg[0].u, 0, n * sizeof(float), ctx->stream));
+    DM_CK(cudaMemsetAsync(tg[0].ph, 0, 4 * slot, ctx->stream));
+    int cs = 0, ct = 0;
+    auto jargs = [&](const St& fin, const St& fout, const St& tin, const St& tout) {
+        dm::JvpArgs j{};
+        j.f = pd_args_st(ctx, fin, fout);
+        j.du = tin.u;
+        j.dph = tin.ph;
+        j.dpv = tin.pv;
+        j.dqh = tin.qh;
+        j.dqv = tin.qv;
+        j.du2 = tout.u;
+        j.dph2 = tout.ph;
+        j.dpv2 = tout.pv;
+        j.dqh2 = tout.qh;
+        j.dqv2 = tout.qv;
+        j.du0 = lin.u;
+        j.ds1 = lin.ph;
+        j.ds2 = lin.pv;
+        j.dlo = lin.qh;
+        j.dhi = lin.qv;
+        j.dcost = d_dcost;
+        j.dalpha = d_dalpha;
+        j.dlambda = (float)dlambda;
+        return j;
+    };
+    const int warps = ctx->p.warps, base = iters / warps, extra = iters % warps;
+    for (int w = 0; w < warps; ++w) {
+        const int nit = base + (w < extra ? 1 : 0);
+        if (nit == 0) continue;
+        DM_CK(dm::launch_lin_jvp(jargs(ws_set(ctx, cs), ws_set(ctx, cs), tg[ct], tg[ct]),
+                                 ctx->stream));
+        ctx->launches += 1;
+        for (int it = 0; it < nit; ++it) {
+            DM_CK(dm::launch_pd_jvp(jargs(ws_set(ctx, cs), ws_set(ctx, cs ^ 1), tg[ct], tg[ct ^ 1]),
+                                    ctx->stream));
+            ctx->launches += 1;
+            cs ^= 1;
+            ct ^= 1;
+        }
+    }
+    DM_CK(cudaMemcpyAsync(d_du, tg[ct].u, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->u_cur = ctx->pq_cur = cs;
     ctx->have_u = true;
     return DM_OK;
 }
@@ -600,7 +1040,7 @@ DM_API int dm_get_cost_volume(dm_ctx* ctx, uint8_t* d_cost, uint8_t* d_wh, uint8
 {
     int rc = ready(ctx);
     if (rc) return rc;
-    if (!ctx->have_cost) return DM_ERR_STATE;
+    if (!ctx->have_cost || (d_cost != nullptr && ctx->cost_f32 != nullptr)) return DM_ERR_STATE;
     const size_t HW = (size_t)ctx->H * ctx->W;
     if (d_cost)
         DM_CK(cudaMemcpyAsync(d_cost, ctx->ws + ctx->lay.cost, HW * ctx->L,

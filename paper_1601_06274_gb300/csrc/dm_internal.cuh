@@ -98,6 +98,81 @@ struct PdArgs {
     float* qv2;
 };
 
+// Reverse of one primal-dual iteration k (pd.cu): state k (u, p, q) and
+// u_{k+1} in, adjoints of the iteration's outputs in, adjoints of its inputs
+// out (ping-pong), per-pixel accumulators updated in place.
+struct AdjArgs {
+    int H, W, L;
+    const uint8_t* wh;
+    const uint8_t* wv;
+    float lambda_r, tau, sigma, h, ap, bp, bq;
+    const float* u;          // state k
+    const float* un;         // u_{k+1}
+    const float* ph;
+    const float* pv;
+    const float* qh;
+    const float* qv;
+    const float* u0;         // linearisation of the warp
+    const float* s1;
+    const float* s2;
+    const float* lo;
+    const float* hi;
+    const float* ub;         // adjoints of u_{k+1}, p_{k+1}, q_{k+1}
+    const float* phb;
+    const float* pvb;
+    const float* qhb;
+    const float* qvb;
+    float* ub2;              // adjoints of u_k, p_k, q_k
+    float* phb2;
+    float* pvb2;
+    float* qhb2;
+    float* qvb2;
+    float* gu0;              // adjoint of the linearisation point (through u0, lo, hi)
+    float* gs1;              // adjoints of the slopes after the convexity fix
+    float* gs2;
+    float* glam;             // d loss / d lambda_r, per pixel (its two edges)
+};
+
+// Reverse of the linearisation of one warp (pd.cu)
+struct LinAdjArgs {
+    int H, W, L;
+    const uint8_t* cost;
+    const float* costf;
+    const float* alpha_px;
+    float alpha, h;
+    const float* u0;         // the warp's linearisation point
+    float* gu0;
+    float* gs1;
+    float* gs2;
+    float* ub;               // adjoint of u at the warp start (accumulated)
+    float* gcost;            // [H][W][L] (nullable)
+    float* galpha;           // [H][W] (nullable)
+};
+
+// Forward mode of one primal-dual iteration (pd.cu): the forward iteration of
+// f and, on the same branches, the tangents of its outputs.
+struct JvpArgs {
+    PdArgs f;
+    const float* du;         // tangents of u, p, q
+    const float* dph;
+    const float* dpv;
+    const float* dqh;
+    const float* dqv;
+    float* du2;              // tangents written by the iteration
+    float* dph2;
+    float* dpv2;
+    float* dqh2;
+    float* dqv2;
+    float* du0;              // tangents of the linearisation (written by launch_lin_jvp)
+    float* ds1;
+    float* ds2;
+    float* dlo;
+    float* dhi;
+    const float* dcost;      // [H][W][L] tangent of the cost samples (nullable)
+    const float* dalpha;     // [H][W] tangent of alpha (nullable)
+    float dlambda;           // tangent of lambda_r
+};
+
 // dm_abi.cu: row of taps for one omega; returns the window radius or -1
 int penalty_taps(int omega, int L, const dm_params& p, int32_t* row);
 
@@ -126,6 +201,11 @@ cudaError_t launch_theta_h_init(const uint8_t* cost, int32_t* base, void* delta,
 cudaError_t launch_init_u_from_labels(const uint16_t* labels, float* u, int n, cudaStream_t s);
 cudaError_t launch_linearise(const PdArgs& a, cudaStream_t s);
 cudaError_t launch_pd_iter(const PdArgs& a, cudaStream_t s);
+cudaError_t launch_pd_adjoint(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_lin_adjoint(const LinAdjArgs& a, cudaStream_t s);
+cudaError_t launch_lin_jvp(const JvpArgs& a, cudaStream_t s);
+cudaError_t launch_pd_jvp(const JvpArgs& a, cudaStream_t s);
+cudaError_t launch_sum_f32(const float* x, int n, double* partial, double* out, cudaStream_t s);
 cudaError_t launch_zero_f32(float* p, size_t n, cudaStream_t s);
 cudaError_t launch_energy(const PdArgs& a, double eps, double delta, double C, double* partial,
                           int nblocks, cudaStream_t s);

@@ -23,29 +23,50 @@ namespace {
 
 constexpr int kTX = 32, kTY = 8;
 
-__device__ __forceinline__ float cost_at(const PdArgs& A, size_t i)
+__device__ __forceinline__ float cost_sample(const uint8_t* c8, const float* cf, size_t i)
 {
-    return A.costf != nullptr ? __ldg(A.costf + i) : (float)__ldg(A.cost + i);
+    return cf != nullptr ? __ldg(cf + i) : (float)__ldg(c8 + i);
 }
+
+// The forward iteration and its reverse (below) recompute the same quantities
+// and must take the same branches on them, so every rounding in these helpers
+// is explicit (no contraction into fused multiply-adds left to the compiler).
 
 // D_i(x): linear interpolation of the cost samples of pixel px with the argument
 // clamped to [0, L-1]
-__device__ __forceinline__ float interp(const PdArgs& A, size_t px, float x)
+__device__ __forceinline__ float interp(const uint8_t* c8, const float* cf, int L, size_t px, float x)
 {
-    const int L = A.L;
     x = fminf(fmaxf(x, 0.0f), (float)(L - 1));
     int k = (int)floorf(x);
     if (k > L - 2) k = L - 2;
     if (k < 0) k = 0;
-    const float t = x - (float)k;
-    const float c0 = cost_at(A, px * L + k);
-    const float c1 = cost_at(A, px * L + k + 1);
-    return c0 + t * (c1 - c0);
+    const float t = __fsub_rn(x, (float)k);
+    const float c0 = cost_sample(c8, cf, px * L + k);
+    const float c1 = cost_sample(c8, cf, px * L + k + 1);
+    return __fmaf_rn(t, __fsub_rn(c1, c0), c0);
 }
 
-__device__ __forceinline__ float alpha_at(const PdArgs& A, int i)
+__device__ __forceinline__ float alpha_of(const float* alpha_px, float alpha, int i)
 {
-    return A.alpha_px != nullptr ? __ldg(A.alpha_px + i) : A.alpha;
+    return alpha_px != nullptr ? __ldg(alpha_px + i) : alpha;
+}
+
+// The linearisation of Sec. 3.1 at u0: interpolated costs at u0 - h, u0, u0 + h
+// and the two slopes before the convexity fix.
+struct LinPx {
+    float dm, d0, dp, s1, s2;
+};
+
+__device__ __forceinline__ LinPx lin_px(const uint8_t* c8, const float* cf, int L, size_t px,
+                                        float al, float u0, float h)
+{
+    LinPx r;
+    r.d0 = interp(c8, cf, L, px, u0);
+    r.dm = interp(c8, cf, L, px, __fsub_rn(u0, h));
+    r.dp = interp(c8, cf, L, px, __fadd_rn(u0, h));
+    r.s1 = __fdiv_rn(__fmul_rn(al, __fsub_rn(r.d0, r.dm)), h);
+    r.s2 = __fdiv_rn(__fmul_rn(al, __fsub_rn(r.dp, r.d0)), h);
+    return r;
 }
 
 __global__ void init_u_kernel(const uint16_t* __restrict__ labels, float* __restrict__ u, int n)
@@ -69,21 +90,17 @@ __global__ void linearise_kernel(const PdArgs A)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float u0 = A.u[i];
-    const float d0 = interp(A, i, u0);
-    const float dm = interp(A, i, u0 - A.h);
-    const float dp = interp(A, i, u0 + A.h);
-    const float al = alpha_at(A, i);
-    float s1 = al * (d0 - dm) / A.h;
-    float s2 = al * (dp - d0) / A.h;
+    const LinPx l = lin_px(A.cost, A.costf, A.L, i, alpha_of(A.alpha_px, A.alpha, i), u0, A.h);
+    float s1 = l.s1, s2 = l.s2;
     if (s2 < s1) {
-        s1 = 0.5f * (s1 + s2);
+        s1 = 0.5f * __fadd_rn(s1, s2);
         s2 = s1;
     }
     A.u0[i] = u0;
     A.s1[i] = s1;
     A.s2[i] = s2;
-    A.lo[i] = fmaxf(u0 - A.h, 0.0f);
-    A.hi[i] = fminf(u0 + A.h, (float)(A.L - 1));
+    A.lo[i] = fmaxf(__fsub_rn(u0, A.h), 0.0f);
+    A.hi[i] = fminf(__fadd_rn(u0, A.h), (float)(A.L - 1));
 }
 
 // prox of step * (omega r_{a,b})*: identity on |t| <= a omega, else shrink by
@@ -91,29 +108,93 @@ __global__ void linearise_kernel(const PdArgs A)
 __device__ __forceinline__ float prox_conj(float t, float omega, float a, float b, float step)
 {
     const float at = fabsf(t);
+    const float ao = __fmul_rn(a, omega);
     float v = t;
-    if (at > a * omega) v = copysignf(fmaxf(a * omega, at - b * step), t);
+    if (at > ao) v = copysignf(fmaxf(ao, __fmaf_rn(-b, step, at)), t);
     return fminf(fmaxf(v, -omega), omega);
+}
+
+// derivatives of prox_conj in t and in omega.  A tie goes to the branch whose
+// derivative in t is zero: at |t| = a omega the value is the same on both
+// branches, and for a omega = 0 the map is constant around t = 0.
+__device__ __forceinline__ void prox_conj_d(float t, float omega, float a, float b, float step,
+                                            float* dt, float* dom)
+{
+    const float at = fabsf(t);
+    const float ao = __fmul_rn(a, omega);
+    float v = t, d = 1.0f, g = 0.0f;
+    if (at >= ao) {
+        const float m = __fmaf_rn(-b, step, at);
+        const float s = t > 0.0f ? 1.0f : (t < 0.0f ? -1.0f : 0.0f);
+        if (m > ao) {
+            v = s * m;
+        } else {
+            v = s * ao;
+            d = 0.0f;
+            g = s * a;
+        }
+    }
+    if (v > omega) {
+        d = 0.0f;
+        g = 1.0f;
+    } else if (v < -omega) {
+        d = 0.0f;
+        g = -1.0f;
+    }
+    *dt = d;
+    *dom = g;
+}
+
+// arguments of the q and p proxes on the edge (i, j)
+__device__ __forceinline__ float q_arg(float q, float tau, float ui, float uj)
+{
+    return __fmaf_rn(tau, __fsub_rn(ui, uj), q);
+}
+
+__device__ __forceinline__ float p_arg(float p, float sigma, float ui, float uni, float uj, float unj)
+{
+    const float ei = __fmaf_rn(2.0f, uni, -ui), ej = __fmaf_rn(2.0f, unj, -uj);
+    return __fmaf_rn(sigma, __fsub_rn(ei, ej), p);
+}
+
+// u_hat = u - tau A^T (p - q) at pixel (x, y)
+__device__ __forceinline__ float u_hat(const float* u, const float* ph, const float* pv,
+                                       const float* qh, const float* qv, int W, int H, int x, int y,
+                                       float tau)
+{
+    const int i = y * W + x;
+    float div = 0.0f;
+    if (x + 1 < W) div = __fadd_rn(div, __fsub_rn(ph[i], qh[i]));
+    if (x > 0) div = __fsub_rn(div, __fsub_rn(ph[i - 1], qh[i - 1]));
+    if (y + 1 < H) div = __fadd_rn(div, __fsub_rn(pv[i], qv[i]));
+    if (y > 0) div = __fsub_rn(div, __fsub_rn(pv[i - W], qv[i - W]));
+    return __fmaf_rn(-tau, div, u[i]);
+}
+
+// prox of tau times the linearised data term before the box clamp; *cs is the
+// case taken: 0 above the kink, 1 below it, 2 at the kink u0
+__device__ __forceinline__ float prox_lin(float uh, float u0, float s1, float s2, float tau, int* cs)
+{
+    const float ts1 = __fmul_rn(tau, s1), ts2 = __fmul_rn(tau, s2);
+    if (uh > __fadd_rn(u0, ts2)) {
+        *cs = 0;
+        return __fsub_rn(uh, ts2);
+    }
+    if (uh < __fadd_rn(u0, ts1)) {
+        *cs = 1;
+        return __fsub_rn(uh, ts1);
+    }
+    *cs = 2;
+    return u0;
 }
 
 // u+ at pixel (x, y) from the old state
 __device__ __forceinline__ float u_step(const PdArgs& A, int x, int y)
 {
-    const int W = A.W;
-    const int i = y * W + x;
-    float div = 0.0f;  // (A^T (p - q))_i
-    if (x + 1 < W) div += A.ph[i] - A.qh[i];
-    if (x > 0) div -= A.ph[i - 1] - A.qh[i - 1];
-    if (y + 1 < A.H) div += A.pv[i] - A.qv[i];
-    if (y > 0) div -= A.pv[i - W] - A.qv[i - W];
-    const float uh = A.u[i] - A.tau * div;
-    const float u0 = A.u0[i];
-    const float ts1 = A.tau * A.s1[i];
-    const float ts2 = A.tau * A.s2[i];
-    float v;
-    if (uh > u0 + ts2) v = uh - ts2;
-    else if (uh < u0 + ts1) v = uh - ts1;
-    else v = u0;
+    const int i = y * A.W + x;
+    int cs;
+    const float v = prox_lin(u_hat(A.u, A.ph, A.pv, A.qh, A.qv, A.W, A.H, x, y, A.tau), A.u0[i],
+                             A.s1[i], A.s2[i], A.tau, &cs);
     return fminf(fmaxf(v, A.lo[i]), A.hi[i]);
 }
 
@@ -139,20 +220,19 @@ __global__ void __launch_bounds__(kTX * kTY) pd_fused_kernel(const PdArgs A)
     const float ui = s_u[ly][lx];
     const float uni = s_un[ly][lx];
     A.u_new[i] = uni;
-    const float ei = 2.0f * uni - ui;
     if (x + 1 < W) {
-        const float om = A.lambda_r * (float)A.wh[i];
+        const float om = __fmul_rn(A.lambda_r, (float)A.wh[i]);
         const float uj = s_u[ly][lx + 1];
-        const float ej = 2.0f * s_un[ly][lx + 1] - uj;
-        A.qh2[i] = prox_conj(A.qh[i] + A.tau * (ui - uj), om, 0.0f, A.bq, A.tau);
-        A.ph2[i] = prox_conj(A.ph[i] + A.sigma * (ei - ej), om, A.ap, A.bp, A.sigma);
+        A.qh2[i] = prox_conj(q_arg(A.qh[i], A.tau, ui, uj), om, 0.0f, A.bq, A.tau);
+        A.ph2[i] = prox_conj(p_arg(A.ph[i], A.sigma, ui, uni, uj, s_un[ly][lx + 1]), om, A.ap, A.bp,
+                             A.sigma);
     }
     if (y + 1 < H) {
-        const float om = A.lambda_r * (float)A.wv[i];
+        const float om = __fmul_rn(A.lambda_r, (float)A.wv[i]);
         const float uj = s_u[ly + 1][lx];
-        const float ej = 2.0f * s_un[ly + 1][lx] - uj;
-        A.qv2[i] = prox_conj(A.qv[i] + A.tau * (ui - uj), om, 0.0f, A.bq, A.tau);
-        A.pv2[i] = prox_conj(A.pv[i] + A.sigma * (ei - ej), om, A.ap, A.bp, A.sigma);
+        A.qv2[i] = prox_conj(q_arg(A.qv[i], A.tau, ui, uj), om, 0.0f, A.bq, A.tau);
+        A.pv2[i] = prox_conj(p_arg(A.pv[i], A.sigma, ui, uni, uj, s_un[ly + 1][lx]), om, A.ap, A.bp,
+                             A.sigma);
     }
 }
 
@@ -177,7 +257,7 @@ __global__ void energy_kernel(const PdArgs A, double eps, double delta, double C
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int x = i % A.W, y = i / A.W;
         const float* u = A.u;
-        acc += (double)alpha_at(A, i) * (double)interp(A, i, u[i]);
+        acc += (double)alpha_of(A.alpha_px, A.alpha, i) * (double)interp(A.cost, A.costf, A.L, i, u[i]);
         if (x + 1 < A.W)
             acc += (double)A.lambda_r * A.wh[i] * r_dc((double)u[i] - (double)u[i + 1], eps, delta, C);
         if (y + 1 < A.H)
@@ -190,6 +270,342 @@ __global__ void energy_kernel(const PdArgs A, double eps, double delta, double C
         __syncthreads();
     }
     if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// ---------------------------------------------------------------------------
+// Reverse mode of the unrolled iteration (the differentiable refinement).
+//
+// Iteration k maps (u, p, q) to (u+, p+, q+) with
+//   u+ = clamp_[lo,hi](prox_lin(u - tau A^T (p - q)))
+//   q+ = prox_q(q + tau A u),   p+ = prox_p(p + sigma A (2u+ - u)).
+// Given the adjoints (ub, pb, qb) of the outputs, the adjoints of the inputs are
+//   tq = qb * dprox_q,  tp = pb * dprox_p                    (per edge)
+//   ubar+ = ub + 2 sigma A^T tp,  uhb = ubar+ * dprox_lin     (per pixel)
+//   ub' = uhb - sigma A^T tp + tau A^T tq
+//   pb' = tp - tau A uhb,  qb' = tq + tau A uhb              (per edge)
+// and the linearisation constants collect ubar+ on the branch the prox took.
+// One kernel per iteration: a 32x8 tile computes tp, tq on its edges and on the
+// edges entering it, then the pixel adjoints on the tile and a one-pixel halo
+// to the right and below, then the dual adjoints of its own edges.
+
+constexpr int kEX = kTX + 2, kEY = kTY + 2;  // edges owned by x0-1 .. x0+kTX, y0-1 .. y0+kTY
+constexpr int kPX = kTX + 1, kPY = kTY + 1;  // pixels x0 .. x0+kTX, y0 .. y0+kTY
+
+__global__ void __launch_bounds__(kTX * kTY) pd_adjoint_kernel(const AdjArgs A)
+{
+    __shared__ float s_tph[kEY][kEX], s_tpv[kEY][kEX], s_tqh[kEY][kEX], s_tqv[kEY][kEX];
+    __shared__ float s_uhb[kPY][kPX];
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int W = A.W, H = A.H;
+    for (int t = threadIdx.x; t < kEX * kEY; t += kTX * kTY) {
+        const int lx = t % kEX, ly = t / kEX;
+        const int x = x0 - 1 + lx, y = y0 - 1 + ly;
+        float tph = 0.0f, tpv = 0.0f, tqh = 0.0f, tqv = 0.0f;
+        if (x >= 0 && y >= 0 && x < W && y < H) {
+            const int i = y * W + x;
+            const float ui = A.u[i], uni = A.un[i];
+            float gl = 0.0f, d, g;
+            if (x + 1 < W) {
+                const float w = (float)A.wh[i];
+                const float om = __fmul_rn(A.lambda_r, w);
+                const float uj = A.u[i + 1];
+                prox_conj_d(q_arg(A.qh[i], A.tau, ui, uj), om, 0.0f, A.bq, A.tau, &d, &g);
+                const float bq = A.qhb[i];
+                tqh = bq * d;
+                gl += bq * g * w;
+                prox_conj_d(p_arg(A.ph[i], A.sigma, ui, uni, uj, A.un[i + 1]), om, A.ap, A.bp,
+                            A.sigma, &d, &g);
+                const float bp = A.phb[i];
+                tph = bp * d;
+                gl += bp * g * w;
+            }
+            if (y + 1 < H) {
+                const float w = (float)A.wv[i];
+                const float om = __fmul_rn(A.lambda_r, w);
+                const float uj = A.u[i + W];
+                prox_conj_d(q_arg(A.qv[i], A.tau, ui, uj), om, 0.0f, A.bq, A.tau, &d, &g);
+                const float bq = A.qvb[i];
+                tqv = bq * d;
+                gl += bq * g * w;
+                prox_conj_d(p_arg(A.pv[i], A.sigma, ui, uni, uj, A.un[i + W]), om, A.ap, A.bp,
+                            A.sigma, &d, &g);
+                const float bp = A.pvb[i];
+                tpv = bp * d;
+                gl += bp * g * w;
+            }
+            if (lx >= 1 && lx <= kTX && ly >= 1 && ly <= kTY) A.glam[i] += gl;
+        }
+        s_tph[ly][lx] = tph;
+        s_tpv[ly][lx] = tpv;
+        s_tqh[ly][lx] = tqh;
+        s_tqv[ly][lx] = tqv;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kPX * kPY; t += kTX * kTY) {
+        const int lx = t % kPX, ly = t / kPX;
+        const int x = x0 + lx, y = y0 + ly;
+        float uhb = 0.0f;
+        if (x < W && y < H) {
+            const int i = y * W + x;
+            const int ex = lx + 1, ey = ly + 1;
+            const float atp = s_tph[ey][ex] - s_tph[ey][ex - 1] + s_tpv[ey][ex] - s_tpv[ey - 1][ex];
+            const float atq = s_tqh[ey][ex] - s_tqh[ey][ex - 1] + s_tqv[ey][ex] - s_tqv[ey - 1][ex];
+            const float wbar = A.sigma * atp;
+            const float unb = A.ub[i] + 2.0f * wbar;
+            const float u0 = A.u0[i];
+            int cs;
+            const float v = prox_lin(u_hat(A.u, A.ph, A.pv, A.qh, A.qv, W, H, x, y, A.tau), u0,
+                                     A.s1[i], A.s2[i], A.tau, &cs);
+            float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+            if (v < A.lo[i]) {
+                if (__fsub_rn(u0, A.h) > 0.0f) g0 = unb;      // lo = u0 - h
+            } else if (v > A.hi[i]) {
+                if (__fadd_rn(u0, A.h) < (float)(A.L - 1)) g0 = unb;  // hi = u0 + h
+            } else if (cs == 0) {
+                uhb = unb;
+                g2 = -A.tau * unb;
+            } else if (cs == 1) {
+                uhb = unb;
+                g1 = -A.tau * unb;
+            } else {
+                g0 = unb;
+            }
+            if (lx < kTX && ly < kTY) {
+                A.ub2[i] = uhb - wbar + A.tau * atq;
+                A.gu0[i] += g0;
+                A.gs1[i] += g1;
+                A.gs2[i] += g2;
+            }
+        }
+        s_uhb[ly][lx] = uhb;
+    }
+    __syncthreads();
+    const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x >= W || y >= H) return;
+    const int i = y * W + x;
+    const float uhb = s_uhb[ly][lx];
+    float phb = 0.0f, qhb = 0.0f, pvb = 0.0f, qvb = 0.0f;
+    if (x + 1 < W) {
+        const float d = A.tau * (uhb - s_uhb[ly][lx + 1]);
+        phb = s_tph[ly + 1][lx + 1] - d;
+        qhb = s_tqh[ly + 1][lx + 1] + d;
+    }
+    if (y + 1 < H) {
+        const float d = A.tau * (uhb - s_uhb[ly + 1][lx]);
+        pvb = s_tpv[ly + 1][lx + 1] - d;
+        qvb = s_tqv[ly + 1][lx + 1] + d;
+    }
+    A.phb2[i] = phb;
+    A.qhb2[i] = qhb;
+    A.pvb2[i] = pvb;
+    A.qvb2[i] = qvb;
+}
+
+// d D_i(x) / dx of the clamped interpolation (zero outside [0, L-1])
+__device__ __forceinline__ float interp_dx(const uint8_t* c8, const float* cf, int L, size_t px,
+                                           float x)
+{
+    if (x < 0.0f || x > (float)(L - 1)) return 0.0f;
+    int k = (int)floorf(x);
+    if (k > L - 2) k = L - 2;
+    return cost_sample(c8, cf, px * L + k + 1) - cost_sample(c8, cf, px * L + k);
+}
+
+// g += w * d D_i(x) / d c_i
+__device__ __forceinline__ void interp_dc(float* g, int L, float x, float w)
+{
+    x = fminf(fmaxf(x, 0.0f), (float)(L - 1));
+    int k = (int)floorf(x);
+    if (k > L - 2) k = L - 2;
+    if (k < 0) k = 0;
+    const float t = __fsub_rn(x, (float)k);
+    g[k] += w * (1.0f - t);
+    g[k + 1] += w * t;
+}
+
+// Reverse of the linearisation at a warp start: the slope adjoints go through
+// the convexity fix into the data weight, the cost samples and the point u0;
+// the accumulators are cleared for the previous warp.
+__global__ void lin_adjoint_kernel(const LinAdjArgs A)
+{
+    const int n = A.H * A.W;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float u0 = A.u0[i], h = A.h;
+    const float al = alpha_of(A.alpha_px, A.alpha, i);
+    const LinPx l = lin_px(A.cost, A.costf, A.L, i, al, u0, h);
+    float b1 = A.gs1[i], b2 = A.gs2[i];
+    if (l.s2 < l.s1) b1 = b2 = 0.5f * (b1 + b2);
+    const float um = __fsub_rn(u0, h), up = __fadd_rn(u0, h);
+    if (A.galpha != nullptr) A.galpha[i] += (b1 * (l.d0 - l.dm) + b2 * (l.dp - l.d0)) / h;
+    if (A.gcost != nullptr) {
+        float* g = A.gcost + (size_t)i * A.L;
+        interp_dc(g, A.L, u0, al / h * (b1 - b2));
+        interp_dc(g, A.L, um, -al / h * b1);
+        interp_dc(g, A.L, up, al / h * b2);
+    }
+    const float x0 = interp_dx(A.cost, A.costf, A.L, i, u0);
+    const float xm = interp_dx(A.cost, A.costf, A.L, i, um);
+    const float xp = interp_dx(A.cost, A.costf, A.L, i, up);
+    A.ub[i] += A.gu0[i] + al / h * (b1 * (x0 - xm) + b2 * (xp - x0));
+    A.gu0[i] = 0.0f;
+    A.gs1[i] = 0.0f;
+    A.gs2[i] = 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// Forward mode (tangents) of the unrolled iteration, on the branches the
+// forward takes: the directional derivative of u in a direction (dc, dalpha,
+// dlambda, du0).  It is the transpose of the reverse mode above; the pair
+// satisfies <gu, J v> = <J^T gu, v> on any trajectory.
+
+// linearisation of a warp and its tangent (u0 = u at the warp start)
+__global__ void lin_jvp_kernel(const JvpArgs J)
+{
+    const PdArgs& A = J.f;
+    const int n = A.H * A.W;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float u0 = A.u[i], du0 = J.du[i], h = A.h;
+    const float al = alpha_of(A.alpha_px, A.alpha, i);
+    const float dal = J.dalpha != nullptr ? J.dalpha[i] : 0.0f;
+    const LinPx l = lin_px(A.cost, A.costf, A.L, i, al, u0, h);
+    const float um = __fsub_rn(u0, h), up = __fadd_rn(u0, h);
+    float dd0 = interp_dx(A.cost, A.costf, A.L, i, u0) * du0;
+    float ddm = interp_dx(A.cost, A.costf, A.L, i, um) * du0;
+    float ddp = interp_dx(A.cost, A.costf, A.L, i, up) * du0;
+    if (J.dcost != nullptr) {
+        dd0 += interp(nullptr, J.dcost, A.L, i, u0);
+        ddm += interp(nullptr, J.dcost, A.L, i, um);
+        ddp += interp(nullptr, J.dcost, A.L, i, up);
+    }
+    float s1 = l.s1, s2 = l.s2;
+    float ds1 = (dal * (l.d0 - l.dm) + al * (dd0 - ddm)) / h;
+    float ds2 = (dal * (l.dp - l.d0) + al * (ddp - dd0)) / h;
+    if (s2 < s1) {
+        s1 = 0.5f * __fadd_rn(s1, s2);
+        s2 = s1;
+        ds1 = ds2 = 0.5f * (ds1 + ds2);
+    }
+    A.u0[i] = u0;
+    A.s1[i] = s1;
+    A.s2[i] = s2;
+    A.lo[i] = fmaxf(um, 0.0f);
+    A.hi[i] = fminf(up, (float)(A.L - 1));
+    J.du0[i] = du0;
+    J.ds1[i] = ds1;
+    J.ds2[i] = ds2;
+    J.dlo[i] = um > 0.0f ? du0 : 0.0f;
+    J.dhi[i] = up < (float)(A.L - 1) ? du0 : 0.0f;
+}
+
+__global__ void __launch_bounds__(kTX * kTY) pd_jvp_kernel(const JvpArgs J)
+{
+    const PdArgs& A = J.f;
+    __shared__ float s_un[kTY + 1][kTX + 1], s_u[kTY + 1][kTX + 1];
+    __shared__ float s_dun[kTY + 1][kTX + 1], s_du[kTY + 1][kTX + 1];
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int W = A.W, H = A.H;
+    for (int t = threadIdx.x; t < (kTX + 1) * (kTY + 1); t += kTX * kTY) {
+        const int lx = t % (kTX + 1), ly = t / (kTX + 1);
+        const int x = x0 + lx, y = y0 + ly;
+        if (x < W && y < H) {
+            const int i = y * W + x;
+            int cs;
+            const float v = prox_lin(u_hat(A.u, A.ph, A.pv, A.qh, A.qv, W, H, x, y, A.tau), A.u0[i],
+                                     A.s1[i], A.s2[i], A.tau, &cs);
+            float ddiv = 0.0f;
+            if (x + 1 < W) ddiv += J.dph[i] - J.dqh[i];
+            if (x > 0) ddiv -= J.dph[i - 1] - J.dqh[i - 1];
+            if (y + 1 < H) ddiv += J.dpv[i] - J.dqv[i];
+            if (y > 0) ddiv -= J.dpv[i - W] - J.dqv[i - W];
+            const float duh = J.du[i] - A.tau * ddiv;
+            const float un = fminf(fmaxf(v, A.lo[i]), A.hi[i]);
+            float dun;
+            if (v < A.lo[i])
+                dun = J.dlo[i];
+            else if (v > A.hi[i])
+                dun = J.dhi[i];
+            else
+                dun = cs == 0 ? duh - A.tau * J.ds2[i] : (cs == 1 ? duh - A.tau * J.ds1[i] : J.du0[i]);
+            s_un[ly][lx] = un;
+            s_u[ly][lx] = A.u[i];
+            s_dun[ly][lx] = dun;
+            s_du[ly][lx] = J.du[i];
+        }
+    }
+    __syncthreads();
+    const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x >= W || y >= H) return;
+    const int i = y * W + x;
+    const float ui = s_u[ly][lx], uni = s_un[ly][lx];
+    const float dui = s_du[ly][lx], deni = 2.0f * s_dun[ly][lx] - dui;
+    A.u_new[i] = uni;
+    J.du2[i] = s_dun[ly][lx];
+    float d, g;
+    if (x + 1 < W) {
+        const float w = (float)A.wh[i];
+        const float om = __fmul_rn(A.lambda_r, w), dom = J.dlambda * w;
+        const float uj = s_u[ly][lx + 1], duj = s_du[ly][lx + 1];
+        const float tq = q_arg(A.qh[i], A.tau, ui, uj);
+        A.qh2[i] = prox_conj(tq, om, 0.0f, A.bq, A.tau);
+        prox_conj_d(tq, om, 0.0f, A.bq, A.tau, &d, &g);
+        J.dqh2[i] = d * (J.dqh[i] + A.tau * (dui - duj)) + g * dom;
+        const float tp = p_arg(A.ph[i], A.sigma, ui, uni, uj, s_un[ly][lx + 1]);
+        A.ph2[i] = prox_conj(tp, om, A.ap, A.bp, A.sigma);
+        prox_conj_d(tp, om, A.ap, A.bp, A.sigma, &d, &g);
+        const float denj = 2.0f * s_dun[ly][lx + 1] - duj;
+        J.dph2[i] = d * (J.dph[i] + A.sigma * (deni - denj)) + g * dom;
+    } else {
+        J.dqh2[i] = 0.0f;
+        J.dph2[i] = 0.0f;
+    }
+    if (y + 1 < H) {
+        const float w = (float)A.wv[i];
+        const float om = __fmul_rn(A.lambda_r, w), dom = J.dlambda * w;
+        const float uj = s_u[ly + 1][lx], duj = s_du[ly + 1][lx];
+        const float tq = q_arg(A.qv[i], A.tau, ui, uj);
+        A.qv2[i] = prox_conj(tq, om, 0.0f, A.bq, A.tau);
+        prox_conj_d(tq, om, 0.0f, A.bq, A.tau, &d, &g);
+        J.dqv2[i] = d * (J.dqv[i] + A.tau * (dui - duj)) + g * dom;
+        const float tp = p_arg(A.pv[i], A.sigma, ui, uni, uj, s_un[ly + 1][lx]);
+        A.pv2[i] = prox_conj(tp, om, A.ap, A.bp, A.sigma);
+        prox_conj_d(tp, om, A.ap, A.bp, A.sigma, &d, &g);
+        const float denj = 2.0f * s_dun[ly + 1][lx] - duj;
+        J.dpv2[i] = d * (J.dpv[i] + A.sigma * (deni - denj)) + g * dom;
+    } else {
+        J.dqv2[i] = 0.0f;
+        J.dpv2[i] = 0.0f;
+    }
+}
+
+constexpr int kSumThreads = 256, kSumBlocks = 152;
+
+// fixed-order sum of a float array in double: per-block partials, then one block
+__global__ void sum_partial_kernel(const float* __restrict__ x, int n, double* __restrict__ partial)
+{
+    __shared__ double sh[kSumThreads];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        acc += (double)x[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = kSumThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void sum_final_kernel(const double* __restrict__ partial, int nb, double* __restrict__ out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double acc = 0.0;
+        for (int b = 0; b < nb; ++b) acc += partial[b];
+        *out = acc;
+    }
 }
 
 }  // namespace
@@ -224,6 +640,42 @@ cudaError_t launch_pd_iter(const PdArgs& a, cudaStream_t s)
 {
     dim3 grd((a.W + kTX - 1) / kTX, (a.H + kTY - 1) / kTY);
     pd_fused_kernel<<<grd, kTX * kTY, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pd_adjoint(const AdjArgs& a, cudaStream_t s)
+{
+    dim3 grd((a.W + kTX - 1) / kTX, (a.H + kTY - 1) / kTY);
+    pd_adjoint_kernel<<<grd, kTX * kTY, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lin_adjoint(const LinAdjArgs& a, cudaStream_t s)
+{
+    const int n = a.H * a.W;
+    lin_adjoint_kernel<<<(n + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lin_jvp(const JvpArgs& a, cudaStream_t s)
+{
+    const int n = a.f.H * a.f.W;
+    lin_jvp_kernel<<<(n + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pd_jvp(const JvpArgs& a, cudaStream_t s)
+{
+    dim3 grd((a.f.W + kTX - 1) / kTX, (a.f.H + kTY - 1) / kTY);
+    pd_jvp_kernel<<<grd, kTX * kTY, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// partial must hold kSumBlocks doubles
+cudaError_t launch_sum_f32(const float* x, int n, double* partial, double* out, cudaStream_t s)
+{
+    sum_partial_kernel<<<kSumBlocks, kSumThreads, 0, s>>>(x, n, partial);
+    sum_final_kernel<<<1, 32, 0, s>>>(partial, kSumBlocks, out);
     return cudaGetLastError();
 }
 

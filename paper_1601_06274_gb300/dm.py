@@ -75,6 +75,15 @@ def lib() -> ctypes.CDLL:
             "dm_launch_count": [_vp, ctypes.POINTER(ctypes.c_uint64)],
             "dm_discrete_pass_noalloc": [_i, _i, _i, ctypes.POINTER(DmParams), _i, _vp, _vp,
                                          _vp, _vp, _vp, _vp],
+            "dm_set_cost_volume_f32": [_vp, _vp, _vp, _vp],
+            "dm_set_data_weights": [_vp, _vp],
+            "dm_set_lambda_r": [_vp, ctypes.c_double],
+            "dm_tape_bytes": [_vp, _i, _i, ctypes.POINTER(ctypes.c_size_t)],
+            "dm_refine_tape": [_vp, _i, _i, _vp, _vp, ctypes.c_size_t],
+            "dm_refine_backward": [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp],
+            "dm_jvp_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
+            "dm_refine_jvp": [_vp, _i, _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp,
+                              ctypes.c_size_t],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -127,6 +136,7 @@ class Context:
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+        self._tape = None
         _ck(lib().dm_set_stream(self._h, _vp(self.stream.cuda_stream)), "dm_set_stream")
         _ck(lib().dm_bind_workspace(self._h, self._ws.data_ptr(), self.workspace_bytes),
             "dm_bind_workspace")
@@ -233,6 +243,78 @@ class Context:
         _ck(lib().dm_energy(self._h, ctypes.byref(e)), "dm_energy")
         return e.value
 
+    # -- differentiable refinement ---------------------------------------------
+    def _dev_f32(self, a):
+        t = self._torch.as_tensor(a) if isinstance(a, np.ndarray) else a
+        return t.to(self.device, self._torch.float32).contiguous()
+
+    def set_cost_volume_f32(self, cost, wh=None, wv=None):
+        """Borrow a float32 [H][W][L] cost volume (the reference is kept here)."""
+        self._cf = self._dev_f32(cost)
+        if wh is not None:
+            self._wh, self._wv = self._dev_u8(wh), self._dev_u8(wv)
+        _ck(lib().dm_set_cost_volume_f32(self._h, self._cf.data_ptr(),
+                                         _ptr(self._wh) if wh is not None else None,
+                                         _ptr(self._wv) if wh is not None else None),
+            "dm_set_cost_volume_f32")
+        self._tape = None
+
+    def set_data_weights(self, alpha=None):
+        self._alpha = None if alpha is None else self._dev_f32(alpha)
+        _ck(lib().dm_set_data_weights(self._h, _ptr(self._alpha)), "dm_set_data_weights")
+        self._tape = None
+
+    def set_lambda_r(self, value: float):
+        _ck(lib().dm_set_lambda_r(self._h, float(value)), "dm_set_lambda_r")
+        self.params.lambda_r = float(value)
+        self._tape = None
+
+    def tape_bytes(self, iters: int, ckpt_every: int) -> int:
+        n = ctypes.c_size_t()
+        _ck(lib().dm_tape_bytes(self._h, iters, ckpt_every, ctypes.byref(n)), "dm_tape_bytes")
+        return n.value
+
+    def refine_tape(self, iters: int, ckpt_every: int, u0=None, tape=None):
+        """dm_refine with checkpoints; returns the tape (a device uint8 tensor)."""
+        if u0 is not None:
+            self._u0 = self._dev_f32(u0)
+            u0 = self._u0
+        nb = self.tape_bytes(iters, ckpt_every)
+        if tape is None or tape.numel() < nb:
+            tape = self._empty(nb, self._torch.uint8)
+        _ck(lib().dm_refine_tape(self._h, iters, ckpt_every, _ptr(u0), tape.data_ptr(),
+                                 tape.numel()), "dm_refine_tape")
+        self._tape = tape
+        return tape
+
+    def refine_backward(self, gu, tape, cost=True, alpha=True, lam=True, u0=False):
+        """Reverse mode of the last refine_tape: (d cost, d alpha, d lambda_r, d u0),
+        each None unless asked for."""
+        torch = self._torch
+        gu = self._dev_f32(gu)
+        gc = self._empty((self.H, self.W, self.L), torch.float32) if cost else None
+        ga = self._empty((self.H, self.W), torch.float32) if alpha else None
+        gl = self._empty((1,), torch.float64) if lam else None
+        g0 = self._empty((self.H, self.W), torch.float32) if u0 else None
+        _ck(lib().dm_refine_backward(self._h, gu.data_ptr(), tape.data_ptr(), tape.numel(),
+                                     _ptr(gc), _ptr(ga), _ptr(gl), _ptr(g0)),
+            "dm_refine_backward")
+        return gc, ga, gl, g0
+
+    def refine_jvp(self, iters: int, u0=None, du0=None, dcost=None, dalpha=None,
+                   dlambda: float = 0.0):
+        """dm_refine_jvp: refined u (read with disparity()) and its directional
+        derivative in (du0, dcost, dalpha, dlambda)."""
+        n = ctypes.c_size_t()
+        _ck(lib().dm_jvp_bytes(self._h, ctypes.byref(n)), "dm_jvp_bytes")
+        scratch = self._empty(n.value, self._torch.uint8)
+        keep = [None if a is None else self._dev_f32(a) for a in (u0, du0, dcost, dalpha)]
+        du = self._empty((self.H, self.W), self._torch.float32)
+        _ck(lib().dm_refine_jvp(self._h, iters, *[_ptr(a) for a in keep], float(dlambda),
+                                du.data_ptr(), scratch.data_ptr(), n.value), "dm_refine_jvp")
+        self._jvp_keep = (keep, scratch)
+        return du
+
     def launch_count(self) -> int:
         n = ctypes.c_uint64()
         _ck(lib().dm_launch_count(self._h, ctypes.byref(n)), "dm_launch_count")
@@ -252,6 +334,65 @@ def discrete_pass_noalloc(params: DmParams, which: int, cost, wedge, lam_in, lam
                                        _ptr(wedge), _ptr(lam_in), _ptr(lam_out), _ptr(err),
                                        _vp(st) if st else None),
         "dm_discrete_pass_noalloc")
+
+
+_REFINE_FN = None
+
+
+def _refine_function():
+    """torch.autograd.Function over refine_tape / refine_backward (built on first use)."""
+    global _REFINE_FN
+    if _REFINE_FN is not None:
+        return _REFINE_FN
+    import torch
+
+    class RefineFunction(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, cost, alpha, lambda_r, u0, dmctx, iters, ckpt_every):
+            lam = float(lambda_r)
+            dmctx.set_cost_volume_f32(cost.detach())
+            dmctx.set_data_weights(None if alpha is None else alpha.detach())
+            dmctx.set_lambda_r(lam)
+            tape = dmctx.refine_tape(iters, ckpt_every, None if u0 is None else u0.detach())
+            fctx.dm, fctx.tape, fctx.iters, fctx.ckpt = dmctx, tape, iters, ckpt_every
+            fctx.inputs = (cost.detach(), None if alpha is None else alpha.detach(), lam,
+                           None if u0 is None else u0.detach())
+            fctx.lam_like = lambda_r if torch.is_tensor(lambda_r) else None
+            return dmctx.disparity()
+
+        @staticmethod
+        def backward(fctx, gu):
+            dmctx = fctx.dm
+            if dmctx._tape is not fctx.tape:
+                # another forward ran on this context since: rebuild this tape
+                cost, alpha, lam, u0 = fctx.inputs
+                dmctx.set_cost_volume_f32(cost)
+                dmctx.set_data_weights(alpha)
+                dmctx.set_lambda_r(lam)
+                dmctx.refine_tape(fctx.iters, fctx.ckpt, u0, fctx.tape)
+            need = fctx.needs_input_grad
+            gc, ga, gl, g0 = dmctx.refine_backward(gu, fctx.tape, cost=need[0],
+                                                   alpha=need[1], lam=need[2], u0=need[3])
+            if gl is not None and fctx.lam_like is not None:
+                gl = gl.reshape(()).to(fctx.lam_like.device, fctx.lam_like.dtype)
+            elif gl is not None:
+                gl = None
+            return gc, ga, gl, g0, None, None, None
+
+    _REFINE_FN = RefineFunction
+    return _REFINE_FN
+
+
+def refine_differentiable(dmctx: Context, cost, alpha, lambda_r, u0, iters: int,
+                          ckpt_every: int = 20):
+    """Refined disparity u(cost, alpha, lambda_r, u0) as a differentiable torch op.
+
+    cost: [H][W][L] float32 (CUDA), alpha: [H][W] float32 or None (scalar
+    params.alpha), lambda_r: float or 0-d tensor, u0: [H][W] float32 or None
+    (the labels of the last discrete stage).  The edge weights are those already
+    in dmctx.  Gradients come from dm_refine_backward with a checkpoint every
+    ckpt_every iterations."""
+    return _refine_function().apply(cost, alpha, lambda_r, u0, dmctx, iters, ckpt_every)
 
 
 def labels_u16(t) -> np.ndarray:

@@ -99,3 +99,44 @@ def test_error_strings(lib):
     for code in range(1, 8):
         assert dm.error_string(code) not in ("ok", "unknown status")
     assert dm.error_string(99) == "unknown status"
+
+
+def _ctx(lib, H=256, W=512, L=96, **kw):
+    from paper_1601_06274_gb300 import dm
+    p = dm.default_params(**kw)
+    h = ctypes.c_void_p()
+    assert lib.dm_create(H, W, L, ctypes.byref(p), ctypes.byref(h)) == 0
+    return h
+
+
+def test_tape_size_follows_checkpoints_and_warps(lib):
+    h = _ctx(lib)
+    n = ctypes.c_size_t()
+    slot = 256 * 512 * 4
+    # 200 iterations, 5 warps of 40, checkpoint every 20: 10 segments of 20
+    assert lib.dm_tape_bytes(h, 200, 20, ctypes.byref(n)) == 0
+    assert n.value == (10 * 5 + 20 * 5 + 10 + 4) * slot + 8192
+    # checkpoint every 30: segment starts 0 30 40 60 80 90 120 150 160 180
+    assert lib.dm_tape_bytes(h, 200, 30, ctypes.byref(n)) == 0
+    assert n.value == (10 * 5 + 30 * 5 + 14) * slot + 8192
+    # no iterations: the start state only
+    assert lib.dm_tape_bytes(h, 0, 20, ctypes.byref(n)) == 0
+    assert n.value == (5 + 14) * slot + 8192
+    for iters, ck in ((-1, 20), (10, 0), (1 << 21, 20)):
+        assert lib.dm_tape_bytes(h, iters, ck, ctypes.byref(n)) == 1
+    assert lib.dm_destroy(h) == 0
+
+
+def test_differentiable_calls_check_state_without_gpu(lib):
+    from paper_1601_06274_gb300 import dm
+    h = _ctx(lib, 8, 8, 16)
+    # no workspace bound: every call that touches device state refuses
+    assert lib.dm_set_cost_volume_f32(h, 4096, None, None) == dm.DM_ERR_STATE
+    assert lib.dm_set_data_weights(h, None) == dm.DM_ERR_STATE
+    assert lib.dm_refine_tape(h, 10, 5, None, None, 0) == dm.DM_ERR_STATE
+    assert lib.dm_refine_backward(h, 4096, None, 0, None, None, None, None) == dm.DM_ERR_STATE
+    assert lib.dm_set_lambda_r(h, -1.0) == dm.DM_ERR_ARG
+    assert lib.dm_set_lambda_r(h, float("nan")) == dm.DM_ERR_ARG
+    assert lib.dm_set_lambda_r(h, 2.5) == dm.DM_OK
+    assert lib.dm_set_lambda_r(None, 1.0) == dm.DM_ERR_ARG
+    assert lib.dm_destroy(h) == 0

@@ -236,6 +236,74 @@ def test_refine_gradient_matches_finite_differences():
         assert an == pytest.approx(fd, rel=1e-6, abs=1e-9)
 
 
+def _half_integer_start(labels, L):
+    return np.clip(labels, 4, L - 6) + 0.5
+
+
+def _u0_fd_errors(grad_u0, cost, wh, wv, u0, alpha, gt, iters, lam, n=12, seed=5, h=1e-6):
+    """relative errors of g_u0 . v against central differences in the start u0,
+    on directions whose quotients at h and h/2 agree"""
+    def lossfn(uu):
+        u, _, _ = O.refine(cost, wh, wv, uu, iters, O.Params(warps=3, lambda_r=lam), alpha)
+        return np.abs(u - gt).mean()
+    rng = np.random.default_rng(seed)
+    errs = []
+    for _ in range(n):
+        v = rng.normal(size=u0.shape)
+        q = lambda hh: (lossfn(u0 + hh * v) - lossfn(u0 - hh * v)) / (2 * hh)
+        f1, f2 = q(h), q(h / 2)
+        if abs(f1 - f2) > 1e-6 * max(1.0, abs(f1)):
+            continue
+        errs.append(abs(float((grad_u0 * v).sum()) - f1) / max(abs(f1), 1e-9))
+    return errs
+
+
+def test_refine_gradient_in_the_start_matches_finite_differences():
+    # the start is the argmin labelling moved to the half-integers and kept 4
+    # labels inside the range: the clamped interpolation has its kinks at the
+    # integers, and three warps of half-width 1 then never reach the ends of
+    # the range.  Neighbours with equal labels put the q prox (a = 0) exactly at
+    # t = 0 in the first iteration, where the map is constant around t (its
+    # derivative is 0).
+    # (after a few iterations equal neighbours meet further exact ties, kinks at
+    # the base point that central differences average over; 4 iterations stay
+    # clear of them)
+    cost, wh, wv, u0, alpha, gt = _adjoint_problem(seed=4)
+    u0 = _half_integer_start(u0, cost.shape[2])
+    iters, lam = 4, 1.2
+    P = O.Params(warps=3, lambda_r=lam)
+    _, _, _, _, _, g0 = O.refine_grad(cost, wh, wv, u0, iters, gt, P, alpha, want_u0=True)
+    errs = _u0_fd_errors(g0, cost, wh, wv, u0, alpha, gt, iters, lam)
+    assert len(errs) >= 8 and max(errs) <= 1e-6
+
+
+def test_start_gradient_pin_catches_the_wrong_tie_of_the_dual_prox(tmp_path):
+    src = open(os.path.join(os.path.dirname(O.__file__), "dm_oracle.c")).read()
+    old, new = "if (fabs(t) < a * omega) {", "if (fabs(t) <= a * omega) {"
+    assert old in src
+    mut = tmp_path / "mut.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(mut), "-lm"],
+                   check=True)
+    lib = ctypes.CDLL(str(so))
+    f64p = ctypes.POINTER(ctypes.c_double)
+    lib.or_refine_grad.argtypes = ([ctypes.c_int] * 3 + [f64p] * 5 + [ctypes.c_int,
+                                   ctypes.POINTER(O.ContParams)] + [f64p] * 7)
+    cost, wh, wv, u0, alpha, gt = _adjoint_problem(seed=4)
+    u0 = _half_integer_start(u0, cost.shape[2])
+    H, W, L = cost.shape
+    iters, lam = 4, 1.2
+    cp = O.Params(warps=3, lambda_r=lam).cont()
+    out = [np.zeros((H, W)), np.zeros(1), np.zeros((H, W, L)), np.zeros((H, W)), np.zeros(1),
+           np.zeros((H, W))]
+    p = lambda a: np.ascontiguousarray(a).ctypes.data_as(f64p)
+    lib.or_refine_grad(H, W, L, p(cost), p(alpha), p(wh), p(wv), p(u0), iters, ctypes.byref(cp),
+                       p(gt), *[p(o) for o in out])
+    errs = _u0_fd_errors(out[5], cost, wh, wv, u0, alpha, gt, iters, lam)
+    assert max(errs) > 1e-3
+
+
 ADJ_MUTATIONS = [
     ("extrapolation factor dropped", "double unb = ub[p] + 2.0 * wbar;", "double unb = ub[p] + wbar;"),
     ("data slope sign", "s2b[p] -= tau * unb;", "s2b[p] += tau * unb;"),
@@ -255,7 +323,7 @@ def test_adjoint_pin_catches_planted_mistakes(tmp_path, name, old, new):
     lib = ctypes.CDLL(str(so))
     f64p = ctypes.POINTER(ctypes.c_double)
     lib.or_refine_grad.argtypes = ([ctypes.c_int] * 3 + [f64p] * 5 + [ctypes.c_int,
-                                   ctypes.POINTER(O.ContParams)] + [f64p] * 6)
+                                   ctypes.POINTER(O.ContParams)] + [f64p] * 7)
     cost, wh, wv, u0, alpha, gt = _adjoint_problem()
     H, W, L = cost.shape
     iters, lam = 30, 1.2
@@ -263,10 +331,46 @@ def test_adjoint_pin_catches_planted_mistakes(tmp_path, name, old, new):
     u, loss, gc, ga, gl = np.zeros((H, W)), np.zeros(1), np.zeros((H, W, L)), np.zeros((H, W)), np.zeros(1)
     p = lambda a: np.ascontiguousarray(a).ctypes.data_as(f64p)
     lib.or_refine_grad(H, W, L, p(cost), p(alpha), p(wh), p(wv), p(u0), iters, ctypes.byref(cp),
-                       p(gt), p(u), p(loss), p(gc), p(ga), p(gl))
+                       p(gt), p(u), p(loss), p(gc), p(ga), p(gl), None)
 
     def lossfn(c, a, l):
         uu, _, _ = O.refine(c, wh, wv, u0, iters, O.Params(warps=3, lambda_r=l), a)
         return np.abs(uu - gt).mean()
     pairs = _fd_directions((gc, ga, float(gl[0])), lossfn, cost, alpha, lam, 16, seed=3)
     assert any(abs(an - fd) > 1e-6 * max(abs(fd), 1e-3) for fd, an in pairs), f"not caught: {name}"
+
+
+def test_unrolled_refinement_is_kinked_at_the_1e3_scale_after_many_iterations():
+    """Central differences of the exact (FP64) unrolled refinement along random
+    unit directions in (cost, alpha, lambda_r): after 30 iterations the
+    quotients at h = 1e-3 and h/2 agree to ~1e-8 (the loss is linear at that
+    scale); after 200 iterations they disagree by several percent or more along
+    every direction: the piecewise-linear iteration amplifies perturbations, so
+    finite differences at h = 1e-3 cannot confirm a gradient there."""
+    H, W, L = 32, 64, 96
+    sp = S.make_pair(H, W, L, planes=4, noise_sigma=2.0, seed=0)
+    rng = np.random.default_rng(1)
+    cost = O.cost_volume(sp.left, sp.right, L) + rng.uniform(0, 1, (H, W, L))
+    wh, wv = (w.astype(float) for w in O.edge_weights(sp.left))
+    alpha = rng.uniform(0.5, 1.5, (H, W))
+    u0 = np.clip(np.argmin(cost, 2) + rng.uniform(-0.3, 0.3, (H, W)), 0, L - 1)
+    spread = {}
+    for iters in (30, 200):
+        def lossf(c, a, lam):
+            u = O.refine(c, wh, wv, u0, iters, O.Params(lambda_r=lam), a)[0]
+            return np.abs(u - sp.gt).mean()
+        drng = np.random.default_rng(2)
+        out = []
+        for _ in range(12):
+            v = drng.standard_normal(cost.size + alpha.size + 1)
+            v /= np.linalg.norm(v)
+            vc, va, vl = v[:cost.size].reshape(cost.shape), v[cost.size:-1].reshape(alpha.shape), v[-1]
+
+            def q(h):
+                return (lossf(cost + h * vc, alpha + h * va, 1 + h * vl)
+                        - lossf(cost - h * vc, alpha - h * va, 1 - h * vl)) / (2 * h)
+            a, b = q(1e-3), q(5e-4)
+            out.append(abs(a - b) / abs(a))
+        spread[iters] = np.array(out)
+    assert np.median(spread[30]) < 1e-6
+    assert np.sum(spread[200] > 1e-2) >= 10
