@@ -38,9 +38,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="kitti", choices=["kitti", "diff"],
+    ap.add_argument("--workload", default="kitti", choices=["kitti", "diff", "stream"],
                     help="kitti: the plain method on the 1242x375x128 frame (default); "
-                         "diff: forward + reverse mode of 200 PD iterations at 512x256x96")
+                         "diff: forward + reverse mode of 200 PD iterations at 512x256x96; "
+                         "stream: 60 warm-started frames of 1920x1080x256 (uint16 costs)")
     return ap.parse_args()
 
 
@@ -296,6 +297,177 @@ def run_diff(args):
 
 
 # ---------------------------------------------------------------------------
+# Algorithmic bytes of one Dual MM pass per pixel-label (the dominant kernel)
+# ---------------------------------------------------------------------------
+
+def dmm_pass_bytes(kernel: int, delta_bytes: int, cost_bytes: int, HW: int, L: int) -> dict:
+    """Bytes a pass must move at least.  16-bit kernel: the horizontal pass reads
+    the deltas of c + lambda_v and writes those of lambda_h (plus a 4-byte base
+    per pixel each); the vertical pass reads lambda_h and c and writes c +
+    lambda_v.  int32 kernel: the horizontal pass reads c and lambda_v and writes
+    lambda_h, the vertical pass reads lambda_h and writes lambda_v."""
+    if kernel == 16:
+        return {0: HW * (2 * delta_bytes * L + 8),
+                1: HW * ((2 * delta_bytes + cost_bytes) * L + 8)}
+    return {0: HW * L * (cost_bytes + 8), 1: HW * L * 8}
+
+
+def hbm_peak():
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        return float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def time_passes(ctx, d_left, d_right, iters, reps, flush, stream, warm_prev=None):
+    """Average duration of each Dual MM pass (CUDA events on the context's stream)."""
+    import torch
+    if warm_prev is None:
+        ctx.cost_volume(d_left, d_right)
+    else:
+        ctx.cost_volume(*warm_prev)
+        ctx.discrete(iters)
+        ctx.cost_volume_warm(d_left, d_right)
+    pass_ms = {0: [], 1: []}
+    for _ in range(reps):
+        for it in range(iters):
+            for which in (0, 1):
+                flush.fill_(it & 0xff)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.discrete_pass(which)
+                b.record(stream)
+                pass_ms[which].append((a, b))
+        ctx.reset_duals()
+    torch.cuda.synchronize()
+    return {w: sum(a.elapsed_time(b) for a, b in v) / len(v) for w, v in pass_ms.items()}
+
+
+def roofline_line(ctx, avg, HW, L, cost_bytes, kernel_names):
+    kernel, dbytes = ctx.path()
+    bytes_per = dmm_pass_bytes(kernel, dbytes, cost_bytes, HW, L)
+    dom = max((0, 1), key=lambda w: avg[w])
+    peak, src = hbm_peak()
+    achieved = bytes_per[dom] / (avg[dom] / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": kernel_names[kernel] + (" horizontal" if dom == 0 else " vertical")
+            + " pass", "peak_source": src,
+            "bytes_per_launch": bytes_per[dom],
+            "dual_storage": f"{dbytes}-byte deltas" if kernel == 16 else "int32",
+            "pass_ms": {"horizontal": round(avg[0], 4), "vertical": round(avg[1], 4)}}
+
+
+KERNEL_NAMES = {16: "dmm16_kernel", 32: "dmm_pass_kernel"}
+
+
+# ---------------------------------------------------------------------------
+# Streaming: 60 warm-started frames of 1920x1080x256 with uint16 costs
+# ---------------------------------------------------------------------------
+
+def run_stream(args):
+    import numpy as np
+    import torch
+    from paper_1601_06274_gb300 import build, dm, synthetic as S
+    build.build()
+    dev = torch.device("cuda", 0)
+    spec = S.STREAM
+    H, W, L, NF = spec["H"], spec["W"], spec["L"], spec["frames"]
+    NI, NP = spec["dmm_iters"], spec["pd_iters"]
+    frames = list(S.make_sequence(H, W, L, NF, planes=spec["planes"],
+                                  noise_sigma=spec["noise_sigma"], drift=spec["drift"], seed=0))
+    d_frames = [(torch.from_numpy(f.left).to(dev), torch.from_numpy(f.right).to(dev))
+                for f in frames]
+    ctx = dm.Context(H, W, L, dm.default_params(cost_bytes=2), device=str(dev))
+    stream = ctx.stream
+    d_u = torch.empty((H, W), dtype=torch.float32, device=dev)
+    for k in range(args.warmup):
+        if k == 0:
+            ctx.solve(*d_frames[0], NI, NP, out=d_u)
+        else:
+            ctx.solve_next(*d_frames[k % NF], NI, NP, out=d_u)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(NF)]
+    launches0 = ctx.launch_count()
+    clk = Clocks(0)
+    with torch.cuda.stream(stream):
+        for f in range(NF):
+            evs[f][0].record(stream)
+            if f == 0:
+                ctx.solve(*d_frames[0], NI, NP, out=d_u)      # cold start
+            else:
+                ctx.solve_next(*d_frames[f], NI, NP, out=d_u)  # warm start from frame f - 1
+            evs[f][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = ctx.launch_count() - launches0
+    ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(ms)
+    fps = NF / (tot_ms / 1e3)
+    cold = []
+    for f in range(min(NF, 5)):       # the same frames, each from a cold start
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.solve(*d_frames[f], NI, NP, out=d_u)
+        b.record(stream)
+        cold.append((a, b))
+    torch.cuda.synchronize()
+    cold_ms = sum(a.elapsed_time(b) for a, b in cold) / len(cold)
+    # warm vs cold lower bound after the iterations on one frame
+    ctx.solve(*d_frames[0], NI, NP, out=d_u)
+    ctx.solve_next(*d_frames[1], NI, NP, out=d_u)
+    lb_warm = ctx.lower_bounds(NI)
+    ctx.solve(*d_frames[1], NI, NP, out=d_u)
+    lb_cold = ctx.lower_bounds(NI)
+    # end to end: pinned host frames in, the disparity back to the host, per frame
+    h_frames = [(torch.from_numpy(f.left).pin_memory(), torch.from_numpy(f.right).pin_memory())
+                for f in frames]
+    h_u = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    dl, dr = torch.empty_like(d_frames[0][0]), torch.empty_like(d_frames[0][1])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    with torch.cuda.stream(stream):
+        for f in range(NF):
+            dl.copy_(h_frames[f][0], non_blocking=True)
+            dr.copy_(h_frames[f][1], non_blocking=True)
+            if f == 0:
+                ctx.solve(dl, dr, NI, NP, out=d_u)
+            else:
+                ctx.solve_next(dl, dr, NI, NP, out=d_u)
+            h_u.copy_(d_u, non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_fps = NF / (a.elapsed_time(b) / 1e3)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    avg = time_passes(ctx, *d_frames[1], NI, 1, flush, stream, warm_prev=d_frames[0])
+    roof = roofline_line(ctx, avg, H * W, L, 2, KERNEL_NAMES)
+    line = {
+        "metric": "frames/s (discrete+continuous), 60 warm-started frames of 1920×1080×256",
+        "value": round(fps, 3), "unit": "frames/s", "n_gpus": 1, "steps": NF,
+        "warmup": args.warmup, "ms_per_step": round(tot_ms / NF, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int16x2+int32+f32",
+        "data": "synthetic",
+        "config": {"workload": "stream-1920x1080x256", "H": H, "W": W, "L": L, "frames": NF,
+                   "dmm_iters": NI, "pd_iters": NP, "cost": "uint16",
+                   "warm_start": "lambda_v of the previous frame",
+                   "l2": "inputs larger than L2 (1.06 GB cost volume per frame)"},
+        "latency_ms": {"p50": round(float(np.percentile(ms, 50)), 3),
+                       "p99": round(float(np.percentile(ms, 99)), 3),
+                       "max": round(max(ms), 3), "cold_start_mean": round(cold_ms, 3)},
+        "lower_bound_frame1": {"warm": int(lb_warm[-1]), "cold": int(lb_cold[-1]),
+                               "warm_first_iter": int(lb_warm[0]),
+                               "cold_first_iter": int(lb_cold[0])},
+        "roofline": roof, "cpu_baseline": None,
+        "e2e": {"value": round(e2e_fps, 3), "unit": "frames/s", "h2d_bytes_per_step": 2 * H * W,
+                "d2h_bytes_per_step": 4 * H * W},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -306,6 +478,9 @@ def main():
         return
     if args.workload == "diff":
         run_diff(args)
+        return
+    if args.workload == "stream":
+        run_stream(args)
         return
     import numpy as np
     import torch
@@ -383,35 +558,8 @@ def main():
     e2e_value = units * args.steps * ws / (sum(e_ms) / 1e3) / 1e6
 
     # ---- dominant kernel: one Dual MM pass per launch, CUDA events on the ctx stream
-    ctx.cost_volume(d_left, d_right)
-    pass_ms = {0: [], 1: []}
-    for _ in range(max(1, args.steps // 2)):
-        ctx.reset_duals()
-        for it in range(NI):
-            for which in (0, 1):
-                flush.fill_(it & 0xff)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                ctx.discrete_pass(which)
-                b.record(stream)
-                pass_ms[which].append((a, b))
-    torch.cuda.synchronize()
-    avg = {w: sum(a.elapsed_time(b) for a, b in v) / len(v) for w, v in pass_ms.items()}
-    # algorithmic bytes per launch (int32 duals): horizontal pass reads c (1 B) and
-    # lambda_v (4 B) and writes lambda_h (4 B) per pixel-label; vertical pass reads
-    # lambda_h and writes lambda_v (8 B)
-    bytes_per = {0: 9 * units, 1: 8 * units}
-    dom = max((0, 1), key=lambda w: avg[w])
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peak, peak_src = 6800.0, "fallback"
-    if os.path.exists(peaks_path):
-        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
-    achieved = bytes_per[dom] / (avg[dom] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "dmm_pass_kernel (" + ("horizontal" if dom == 0 else "vertical") + ")",
-                "peak_source": peak_src,
-                "pass_ms": {"horizontal": round(avg[0], 4), "vertical": round(avg[1], 4)}}
+    avg = time_passes(ctx, d_left, d_right, NI, max(1, args.steps // 2), flush, stream)
+    roofline = roofline_line(ctx, avg, H * W, L, 1, KERNEL_NAMES)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -13,8 +13,9 @@
  *
  * Conventions shared by every entry point
  *   - Images are H x W, row-major, uint8, one byte per pixel (no padding).
- *   - The cost volume is [H][W][L] uint8, labels innermost; label l is the
- *     disparity l pixels (right-image pixel x - l).
+ *   - The cost volume is [H][W][L] uint8 (uint16 with params.cost_bytes = 2),
+ *     labels innermost; label l is the disparity l pixels (right-image pixel
+ *     x - l).
  *   - Edge weights omega are [H][W] uint8: wh[y][x] belongs to the edge
  *     (y,x)-(y,x+1), wv[y][x] to (y,x)-(y+1,x); entries without an edge are
  *     ignored.
@@ -84,7 +85,9 @@ typedef struct dm_params {
     int32_t dmm_path;       /* Dual MM kernel: 0 = automatic (packed 16-bit     */
                             /* arithmetic whenever its value bounds hold),       */
                             /* 1 = always the int32 kernel                       */
-    int32_t reserved[6];
+    int32_t cost_bytes;     /* storage of the cost volume: 0 or 1 = uint8,       */
+                            /* 2 = uint16                                        */
+    int32_t reserved[5];
 } dm_params;
 
 typedef struct dm_ctx dm_ctx;
@@ -125,6 +128,27 @@ DM_API int dm_cost_volume(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_r
 DM_API int dm_set_cost_volume(dm_ctx* ctx, const uint8_t* d_cost, const uint8_t* d_wh,
                               const uint8_t* d_wv);
 
+/* Use a caller-made uint16 cost volume (contexts created with
+ * params.cost_bytes = 2; DM_ERR_STATE otherwise) and edge weights, copied into
+ * the workspace.  cost_max bounds the samples (0..65535); the caller
+ * guarantees it.  It selects the Dual MM kernel: the packed 16-bit kernel when
+ * cost_max + 2 (omega C + 1) <= 16257, else the int32 kernel, which needs
+ * (cost_max + 4 omega C) (max(H, W) + 1) < 2^30 (DM_ERR_RANGE otherwise).
+ * Resets the dual variables. */
+DM_API int dm_set_cost_volume_u16(dm_ctx* ctx, const uint16_t* d_cost, const uint8_t* d_wh,
+                                  const uint8_t* d_wv, int cost_max);
+
+/* dm_cost_volume for the next frame of a sequence, keeping the vertical duals
+ * lambda_v of the previous frame as the starting point of Alg. Dual_MM (a warm
+ * start; the paper starts from zero).  The first horizontal pass then uses the
+ * unaries c_new + lambda_v_old; the lower bound returned after a full
+ * iteration is valid for the new frame whatever lambda_v_old was, because each
+ * pass rebuilds its dual from a minorant of the current chains.  Without a
+ * previous cost volume this is dm_cost_volume.  A warm start whose unaries do
+ * not fit the 16-bit kernel's storage is reported as DM_ERR_DEVICE by the
+ * next synchronising call. */
+DM_API int dm_cost_volume_warm(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right);
+
 /* Zero both dual variables (a cold start of Alg. Dual_MM). */
 DM_API int dm_reset_duals(dm_ctx* ctx);
 
@@ -151,6 +175,11 @@ DM_API int dm_refine(dm_ctx* ctx, int iters, const float* d_u0);
 DM_API int dm_solve(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int dmm_iters,
                     int pd_iters, float* d_u);
 
+/* dm_solve for the next frame of a sequence: dm_cost_volume_warm, then the
+ * same iterations (the refinement starts from the new labels). */
+DM_API int dm_solve_next(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right,
+                         int dmm_iters, int pd_iters, float* d_u);
+
 /* Same with host buffers: copies the images in and the disparity (and, if
  * h_labels is not NULL, the labels) out through the workspace; synchronous. */
 DM_API int dm_solve_host(dm_ctx* ctx, const uint8_t* h_left, const uint8_t* h_right,
@@ -161,6 +190,7 @@ DM_API int dm_get_labels(dm_ctx* ctx, uint16_t* d_labels);            /* H*W    
 DM_API int dm_get_disparity(dm_ctx* ctx, float* d_u);                 /* H*W        */
 DM_API int dm_get_duals(dm_ctx* ctx, int32_t* d_lam_h, int32_t* d_lam_v); /* H*W*L each */
 DM_API int dm_get_cost_volume(dm_ctx* ctx, uint8_t* d_cost, uint8_t* d_wh, uint8_t* d_wv);
+                                       /* d_cost: H*W*L*cost_bytes bytes */
 
 /* Lower bounds of the last dm_discrete call (n <= iters of that call);
  * synchronous. */
@@ -267,6 +297,11 @@ DM_API int dm_discrete_pass_noalloc(int H, int W, int L, const dm_params* p, int
                                     const uint8_t* d_cost, const uint8_t* d_wedge,
                                     const int32_t* d_lam_in, int32_t* d_lam_out,
                                     int32_t* d_err, void* stream);
+
+/* The Dual MM kernel chosen for the current cost volume: *kernel = 16 (packed
+ * 16-bit arithmetic, dual deltas of *delta_bytes bytes per label) or 32 (int32
+ * kernel, *delta_bytes = 4).  Host only. */
+DM_API int dm_get_path(const dm_ctx* ctx, int* kernel, int* delta_bytes);
 
 /* Number of kernels this context has enqueued since dm_create (host-side
  * counter; instrumentation for benchmarks). */

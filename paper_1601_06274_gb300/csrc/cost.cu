@@ -54,8 +54,9 @@ __global__ void census_edges_kernel(const uint8_t* __restrict__ left,
     }
 }
 
+template <typename CT>
 __global__ void cost_kernel(const uint32_t* __restrict__ cl, const uint32_t* __restrict__ cr,
-                            int H, int W, int L, int maxc, uint8_t* __restrict__ cost)
+                            int H, int W, int L, int maxc, CT* __restrict__ cost)
 {
     // one thread: pixel p, labels [16 g, 16 g + 16)
     const int groups = (L + 15) >> 4;
@@ -67,23 +68,37 @@ __global__ void cost_kernel(const uint32_t* __restrict__ cl, const uint32_t* __r
     const int x = (int)(p % W);
     const uint32_t a = cl[p];
     const int l0 = g << 4;
-    uint8_t v[16];
+    uint32_t v[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
         const int l = l0 + k;
         const int xr = x - l;
-        v[k] = (uint8_t)(xr >= 0 ? __popc(a ^ cr[p - l]) : maxc);
+        v[k] = xr >= 0 ? (uint32_t)__popc(a ^ cr[p - l]) : (uint32_t)maxc;
     }
-    uint8_t* dst = cost + p * L + l0;
+    CT* dst = cost + p * L + l0;
     if ((L & 15) == 0) {
-        uint4 w;
-        w.x = v[0] | (v[1] << 8) | (v[2] << 16) | ((uint32_t)v[3] << 24);
-        w.y = v[4] | (v[5] << 8) | (v[6] << 16) | ((uint32_t)v[7] << 24);
-        w.z = v[8] | (v[9] << 8) | (v[10] << 16) | ((uint32_t)v[11] << 24);
-        w.w = v[12] | (v[13] << 8) | (v[14] << 16) | ((uint32_t)v[15] << 24);
-        *reinterpret_cast<uint4*>(dst) = w;
+        if constexpr (sizeof(CT) == 1) {
+            uint4 w;
+            w.x = v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24);
+            w.y = v[4] | (v[5] << 8) | (v[6] << 16) | (v[7] << 24);
+            w.z = v[8] | (v[9] << 8) | (v[10] << 16) | (v[11] << 24);
+            w.w = v[12] | (v[13] << 8) | (v[14] << 16) | (v[15] << 24);
+            *reinterpret_cast<uint4*>(dst) = w;
+        } else {
+            uint4 w0, w1;
+            w0.x = v[0] | (v[1] << 16);
+            w0.y = v[2] | (v[3] << 16);
+            w0.z = v[4] | (v[5] << 16);
+            w0.w = v[6] | (v[7] << 16);
+            w1.x = v[8] | (v[9] << 16);
+            w1.y = v[10] | (v[11] << 16);
+            w1.z = v[12] | (v[13] << 16);
+            w1.w = v[14] | (v[15] << 16);
+            reinterpret_cast<uint4*>(dst)[0] = w0;
+            reinterpret_cast<uint4*>(dst)[1] = w1;
+        }
     } else {
-        for (int k = 0; k < 16 && l0 + k < L; ++k) dst[k] = v[k];
+        for (int k = 0; k < 16 && l0 + k < L; ++k) dst[k] = (CT)v[k];
     }
 }
 
@@ -102,14 +117,18 @@ cudaError_t launch_census_edges(const uint8_t* left, const uint8_t* right, int H
     return cudaGetLastError();
 }
 
-cudaError_t launch_cost(const uint32_t* census, int H, int W, int L, int maxc, uint8_t* cost,
-                        cudaStream_t s)
+cudaError_t launch_cost(const uint32_t* census, int H, int W, int L, int maxc, void* cost,
+                        int cost_bytes, cudaStream_t s)
 {
     const long long total = (long long)H * W * ((L + 15) / 16);
     const int threads = 256;
     const long long blocks = (total + threads - 1) / threads;
-    cost_kernel<<<(unsigned)blocks, threads, 0, s>>>(census, census + (size_t)H * W, H, W, L, maxc,
-                                                     cost);
+    if (cost_bytes == 2)
+        cost_kernel<uint16_t><<<(unsigned)blocks, threads, 0, s>>>(
+            census, census + (size_t)H * W, H, W, L, maxc, static_cast<uint16_t*>(cost));
+    else
+        cost_kernel<uint8_t><<<(unsigned)blocks, threads, 0, s>>>(
+            census, census + (size_t)H * W, H, W, L, maxc, static_cast<uint8_t*>(cost));
     return cudaGetLastError();
 }
 

@@ -35,6 +35,8 @@ struct dm_ctx {
     int last_iters = 0;
     unsigned long long launches = 0;  // kernels enqueued by this context
     bool have_weights = false;  // edge weights in the workspace
+    int cost_bytes = 1;         // storage of the cost volume: uint8 or uint16
+    int cost_max = 0;           // bound on the current cost volume's samples
     // differentiable form: a caller's float cost volume and per-pixel data
     // weights (borrowed, nullable) and the tape of the last checkpointed forward
     const float* cost_f32 = nullptr;
@@ -48,6 +50,7 @@ struct dm_ctx {
 namespace {
 
 constexpr int kMaxIters = 4096;
+constexpr int kMaxDelta16 = 255 + 2 * (8000 + 1);  // largest delta the 16-bit kernel admits
 
 #define DM_CK(call)                                  \
     do {                                             \
@@ -114,6 +117,7 @@ bool params_ok(const dm_params& p)
     if (!(p.lambda_r >= 0.0 && p.alpha >= 0.0 && p.tau > 0.0 && p.sigma > 0.0 && p.h > 0.0))
         return false;
     if (p.warps < 1) return false;
+    if (p.cost_bytes < 0 || p.cost_bytes > 2) return false;
     return true;
 }
 
@@ -126,6 +130,7 @@ dm::PdArgs pd_args(dm_ctx* c)
     a.W = c->W;
     a.L = c->L;
     a.cost = ws + l.cost;
+    a.cost16 = c->cost_bytes == 2 ? reinterpret_cast<const uint16_t*>(ws + l.cost) : nullptr;
     a.wh = ws + l.wh;
     a.wv = ws + l.wv;
     a.alpha = (float)c->p.alpha;
@@ -301,6 +306,7 @@ int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
     a.W = c->W;
     a.L = c->L;
     a.cost = ws + c->lay.cost;
+    a.cost16 = c->cost_bytes == 2 ? reinterpret_cast<const uint16_t*>(ws + c->lay.cost) : nullptr;
     a.base_in = reinterpret_cast<const int32_t*>(in);
     a.delta_in = in + base_bytes(c);
     a.base_out = reinterpret_cast<int32_t*>(out);
@@ -323,11 +329,18 @@ int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
     return DM_OK;
 }
 
-// storage of the duals for a new cost volume whose values are <= cost_max
+// kernel and storage of the duals for a new cost volume whose values are <=
+// cost_max: the packed 16-bit kernel needs every dual delta, at most
+// max(c) + 2 (omega C + 1), to stay below its 16-bit infinity; the int32 kernel
+// needs (max(c) + 4 omega C) times the chain length below 2^30
 int choose_path(dm_ctx* c, int cost_max, bool user_weights)
 {
     const int p2 = user_weights ? c->p2_all : c->p2_used;
-    c->use16 = c->can16;
+    const long long n = (c->H > c->W ? c->H : c->W) + 1;
+    if (c->discrete_ok && ((long long)cost_max + 4LL * c->p2_all) * n >= (1LL << 30))
+        return DM_ERR_RANGE;
+    c->cost_max = cost_max;
+    c->use16 = c->can16 && cost_max + 2 * (p2 + 1) <= kMaxDelta16;
     c->delta_bytes = (cost_max + 2 * (p2 + 1) <= 255) ? 1 : 2;
     if (!c->discrete_ok) return DM_OK;  // weights only feed the continuous stage
     DM_CK(dm::launch_validate_edges(c->ws + c->lay.wh, c->ws + c->lay.wv, c->H, c->W,
@@ -348,6 +361,7 @@ int run_pass(dm_ctx* c, int which, uint16_t* labels, long long* lb)
     a.L = c->L;
     a.KP = c->KP;
     a.cost = ws + c->lay.cost;
+    a.cost16 = c->cost_bytes == 2 ? reinterpret_cast<const uint16_t*>(ws + c->lay.cost) : nullptr;
     int32_t* lh = reinterpret_cast<int32_t*>(ws + c->lay.lam_h);
     int32_t* lv = reinterpret_cast<int32_t*>(ws + c->lay.lam_v);
     a.lam_in = which == 0 ? lv : lh;
@@ -362,6 +376,25 @@ int run_pass(dm_ctx* c, int which, uint16_t* labels, long long* lb)
     DM_CK(dm::launch_dmm_pass(a, c->lpt, c->radius, c->stream));
     c->launches += 1;
     return DM_OK;
+}
+
+// census, edge weights and cost volume of a new pair (the duals are left alone)
+int census_cost(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right)
+{
+    uint8_t* ws = ctx->ws;
+    uint32_t* census = reinterpret_cast<uint32_t*>(ws + ctx->lay.census);
+    const int maxc = ctx->p.census_win * ctx->p.census_win - 1;
+    DM_CK(dm::launch_census_edges(d_left, d_right, ctx->H, ctx->W, ctx->p.census_win,
+                                  ctx->p.edge_threshold, ctx->p.w_hi, ctx->p.w_lo, census,
+                                  ws + ctx->lay.wh, ws + ctx->lay.wv, ctx->stream));
+    DM_CK(dm::launch_cost(census, ctx->H, ctx->W, ctx->L, maxc, ws + ctx->lay.cost,
+                          ctx->cost_bytes, ctx->stream));
+    ctx->launches += 2;
+    ctx->have_cost = true;
+    ctx->have_weights = true;
+    ctx->cost_f32 = nullptr;
+    ctx->tape_valid = false;
+    return choose_path(ctx, maxc, false);
 }
 
 }  // namespace
@@ -410,6 +443,7 @@ DM_API int dm_create(int H, int W, int L, const dm_params* p, dm_ctx** out)
     c->W = W;
     c->L = L;
     c->p = *p;
+    c->cost_bytes = p->cost_bytes == 2 ? 2 : 1;
     c->lpt = L <= 32 ? 1 : (L <= 64 ? 2 : (L <= 128 ? 4 : 8));
     c->KP = 32 * c->lpt;
     c->taps.assign(256 * dm::kTapW, 0);
@@ -450,7 +484,7 @@ DM_API int dm_create(int H, int W, int L, const dm_params* p, dm_ctx** out)
         return off;
     };
     const size_t HW = (size_t)H * W, HWL = HW * L;
-    l.cost = add(HWL);
+    l.cost = add(HWL * c->cost_bytes);
     l.census = add(2 * HW * sizeof(uint32_t));
     l.img = add(2 * HW);
     l.wh = add(HW);
@@ -530,6 +564,27 @@ DM_API int dm_set_stream(dm_ctx* ctx, void* stream)
     return DM_OK;
 }
 
+DM_API int dm_set_cost_volume_u16(dm_ctx* ctx, const uint16_t* d_cost, const uint8_t* d_wh,
+                                  const uint8_t* d_wv, int cost_max)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (d_cost == nullptr || d_wh == nullptr || d_wv == nullptr) return DM_ERR_ARG;
+    if (cost_max < 0 || cost_max > 65535 || (reinterpret_cast<uintptr_t>(d_cost) & 1)) return DM_ERR_ARG;
+    if (ctx->cost_bytes != 2) return DM_ERR_STATE;
+    const size_t HW = (size_t)ctx->H * ctx->W;
+    DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.cost, d_cost, HW * ctx->L * sizeof(uint16_t),
+                          cudaMemcpyDeviceToDevice, ctx->stream));
+    DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.wh, d_wh, HW, cudaMemcpyDeviceToDevice, ctx->stream));
+    DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.wv, d_wv, HW, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->have_cost = true;
+    ctx->have_weights = true;
+    ctx->cost_f32 = nullptr;
+    ctx->tape_valid = false;
+    if ((rc = choose_path(ctx, cost_max, true))) return rc;
+    return dm_reset_duals(ctx);
+}
+
 DM_API int dm_reset_duals(dm_ctx* ctx)
 {
     int rc = ready(ctx);
@@ -540,7 +595,8 @@ DM_API int dm_reset_duals(dm_ctx* ctx)
     if (ctx->use16 && ctx->have_cost) {
         // the 16-bit path keeps c + lambda_v in place of lambda_v: c for a cold start
         uint8_t* reg = ctx->ws + ctx->lay.lam_v;
-        DM_CK(dm::launch_theta_h_init(ctx->ws + ctx->lay.cost, reinterpret_cast<int32_t*>(reg),
+        DM_CK(dm::launch_theta_h_init(ctx->ws + ctx->lay.cost, ctx->cost_bytes,
+                                      reinterpret_cast<int32_t*>(reg),
                                       reg + base_bytes(ctx), ctx->delta_bytes,
                                       (long long)ctx->H * ctx->W, ctx->L, ctx->stream));
         ctx->launches += 1;
@@ -554,21 +610,50 @@ DM_API int dm_cost_volume(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_r
     int rc = ready(ctx);
     if (rc) return rc;
     if (d_left == nullptr || d_right == nullptr) return DM_ERR_ARG;
-    uint8_t* ws = ctx->ws;
-    uint32_t* census = reinterpret_cast<uint32_t*>(ws + ctx->lay.census);
-    DM_CK(dm::launch_census_edges(d_left, d_right, ctx->H, ctx->W, ctx->p.census_win,
-                                  ctx->p.edge_threshold, ctx->p.w_hi, ctx->p.w_lo, census,
-                                  ws + ctx->lay.wh, ws + ctx->lay.wv, ctx->stream));
-    DM_CK(dm::launch_cost(census, ctx->H, ctx->W, ctx->L,
-                          ctx->p.census_win * ctx->p.census_win - 1, ws + ctx->lay.cost,
-                          ctx->stream));
-    ctx->launches += 2;
-    ctx->have_cost = true;
-    ctx->have_weights = true;
-    ctx->cost_f32 = nullptr;
-    ctx->tape_valid = false;
-    if ((rc = choose_path(ctx, ctx->p.census_win * ctx->p.census_win - 1, false))) return rc;
+    if ((rc = census_cost(ctx, d_left, d_right))) return rc;
     return dm_reset_duals(ctx);
+}
+
+DM_API int dm_cost_volume_warm(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (d_left == nullptr || d_right == nullptr) return DM_ERR_ARG;
+    const bool warm = ctx->have_cost && ctx->cost_f32 == nullptr && ctx->discrete_ok;
+    if (!warm) return dm_cost_volume(ctx, d_left, d_right);
+    const long long n_px = (long long)ctx->H * ctx->W;
+    uint8_t* reg = ctx->ws + ctx->lay.lam_v;
+    int32_t* lam_v32 = reinterpret_cast<int32_t*>(ctx->ws + ctx->lay.lam_h);
+    const bool was16 = ctx->use16;
+    if (was16) {
+        // lambda_v = (c + lambda_v) - c with the previous frame's c, as int32 in the
+        // lambda_h region (the next horizontal pass overwrites it)
+        DM_CK(dm::launch_duals_to_i32(reinterpret_cast<const int32_t*>(reg), reg + base_bytes(ctx),
+                                      ctx->delta_bytes, ctx->ws + ctx->lay.cost, ctx->cost_bytes,
+                                      n_px, ctx->L, lam_v32, ctx->stream));
+        ctx->launches += 1;
+    }
+    if ((rc = census_cost(ctx, d_left, d_right))) return rc;
+    if (ctx->use16) {
+        const int32_t* src = was16 ? lam_v32 : reinterpret_cast<const int32_t*>(reg);
+        if (!was16) {
+            // int32 lambda_v -> the lambda_h region, then c + lambda_v into place
+            DM_CK(cudaMemcpyAsync(lam_v32, reg, (size_t)n_px * ctx->L * sizeof(int32_t),
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+            src = lam_v32;
+        }
+        DM_CK(dm::launch_theta_h_from_i32(src, ctx->ws + ctx->lay.cost, ctx->cost_bytes,
+                                          reinterpret_cast<int32_t*>(reg), reg + base_bytes(ctx),
+                                          ctx->delta_bytes, n_px, ctx->L,
+                                          reinterpret_cast<int32_t*>(ctx->ws + ctx->lay.err),
+                                          ctx->stream));
+        ctx->launches += 1;
+    } else if (was16) {
+        DM_CK(cudaMemcpyAsync(reg, lam_v32, (size_t)n_px * ctx->L * sizeof(int32_t),
+                              cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    ctx->have_labels = false;
+    return DM_OK;
 }
 
 DM_API int dm_set_cost_volume(dm_ctx* ctx, const uint8_t* d_cost, const uint8_t* d_wh,
@@ -577,6 +662,7 @@ DM_API int dm_set_cost_volume(dm_ctx* ctx, const uint8_t* d_cost, const uint8_t*
     int rc = ready(ctx);
     if (rc) return rc;
     if (d_cost == nullptr || d_wh == nullptr || d_wv == nullptr) return DM_ERR_ARG;
+    if (ctx->cost_bytes != 1) return DM_ERR_STATE;
     const size_t HW = (size_t)ctx->H * ctx->W;
     DM_CK(cudaMemcpyAsync(ctx->ws + ctx->lay.cost, d_cost, HW * ctx->L, cudaMemcpyDeviceToDevice,
                           ctx->stream));
@@ -869,6 +955,7 @@ DM_API int dm_refine_backward(dm_ctx* ctx, const float* d_gu, void* d_tape, size
             b.W = ctx->W;
             b.L = ctx->L;
             b.cost = P.cost;
+            b.cost16 = P.cost16;
             b.costf = P.costf;
             b.alpha_px = P.alpha_px;
             b.alpha = P.alpha;
@@ -1020,9 +1107,10 @@ DM_API int dm_get_duals(dm_ctx* ctx, int32_t* d_lam_h, int32_t* d_lam_v)
         for (int t = 0; t < 2; ++t) {
             if (dst[t] == nullptr) continue;
             const uint8_t* reg = ctx->ws + lay[t];
-            DM_CK(dm::launch_duals_to_i32(reinterpret_cast<const int32_t*>(reg), reg + base_bytes(ctx),
-                                          ctx->delta_bytes, t == 1 ? ctx->ws + ctx->lay.cost : nullptr,
-                                          npx, ctx->L, dst[t], ctx->stream));
+            DM_CK(dm::launch_duals_to_i32(reinterpret_cast<const int32_t*>(reg),
+                                          reg + base_bytes(ctx), ctx->delta_bytes,
+                                          t == 1 ? ctx->ws + ctx->lay.cost : nullptr,
+                                          ctx->cost_bytes, npx, ctx->L, dst[t], ctx->stream));
             ctx->launches += 1;
         }
         return DM_OK;
@@ -1043,7 +1131,7 @@ DM_API int dm_get_cost_volume(dm_ctx* ctx, uint8_t* d_cost, uint8_t* d_wh, uint8
     if (!ctx->have_cost || (d_cost != nullptr && ctx->cost_f32 != nullptr)) return DM_ERR_STATE;
     const size_t HW = (size_t)ctx->H * ctx->W;
     if (d_cost)
-        DM_CK(cudaMemcpyAsync(d_cost, ctx->ws + ctx->lay.cost, HW * ctx->L,
+        DM_CK(cudaMemcpyAsync(d_cost, ctx->ws + ctx->lay.cost, HW * ctx->L * ctx->cost_bytes,
                               cudaMemcpyDeviceToDevice, ctx->stream));
     if (d_wh)
         DM_CK(cudaMemcpyAsync(d_wh, ctx->ws + ctx->lay.wh, HW, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1095,6 +1183,17 @@ DM_API int dm_solve(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, 
     return DM_OK;
 }
 
+DM_API int dm_solve_next(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right,
+                         int dmm_iters, int pd_iters, float* d_u)
+{
+    int rc;
+    if ((rc = dm_cost_volume_warm(ctx, d_left, d_right))) return rc;
+    if ((rc = dm_discrete(ctx, dmm_iters, nullptr))) return rc;
+    if ((rc = dm_refine(ctx, pd_iters, nullptr))) return rc;
+    if (d_u != nullptr && (rc = dm_get_disparity(ctx, d_u))) return rc;
+    return DM_OK;
+}
+
 DM_API int dm_solve_host(dm_ctx* ctx, const uint8_t* h_left, const uint8_t* h_right,
                          int dmm_iters, int pd_iters, float* h_u, uint16_t* h_labels)
 {
@@ -1112,6 +1211,14 @@ DM_API int dm_solve_host(dm_ctx* ctx, const uint8_t* h_left, const uint8_t* h_ri
         DM_CK(cudaMemcpyAsync(h_labels, ctx->ws + ctx->lay.labels, HW * sizeof(uint16_t),
                               cudaMemcpyDeviceToHost, ctx->stream));
     return check_device_error(ctx);
+}
+
+DM_API int dm_get_path(const dm_ctx* ctx, int* kernel, int* delta_bytes)
+{
+    if (ctx == nullptr || kernel == nullptr || delta_bytes == nullptr) return DM_ERR_ARG;
+    *kernel = ctx->use16 ? 16 : 32;
+    *delta_bytes = ctx->use16 ? ctx->delta_bytes : 4;
+    return DM_OK;
 }
 
 DM_API int dm_launch_count(const dm_ctx* ctx, uint64_t* count)

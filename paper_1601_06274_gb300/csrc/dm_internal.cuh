@@ -35,7 +35,8 @@ struct Layout {
 struct DmmArgs {
     int which;              // 0 horizontal chains (rows), 1 vertical chains (columns)
     int H, W, L, KP;        // KP: labels padded to 32 * LPT
-    const uint8_t* cost;    // [H][W][L]
+    const uint8_t* cost;    // [H][W][L] uint8, or
+    const uint16_t* cost16; // [H][W][L] uint16 when not null
     const int32_t* lam_in;  // lambda_v (which = 0) or lambda_h (which = 1)
     int32_t* lam_out;       // lambda_h (which = 0) or lambda_v (which = 1)
     const uint8_t* wedge;   // wh (which = 0) or wv (which = 1)
@@ -56,6 +57,7 @@ struct DmmArgs {
 struct Dmm16Args {
     int which, H, W, L;
     const uint8_t* cost;
+    const uint16_t* cost16;  // used in place of cost when not null
     const int32_t* base_in;
     const void* delta_in;
     int32_t* base_out;
@@ -74,7 +76,8 @@ struct Dmm16Args {
 
 struct PdArgs {
     int H, W, L;
-    const uint8_t* cost;     // [H][W][L] uint8 samples, used when costf is null
+    const uint8_t* cost;     // [H][W][L] uint8 samples, used when the others are null
+    const uint16_t* cost16;  // [H][W][L] uint16 samples (nullable)
     const float* costf;      // [H][W][L] float32 samples (nullable)
     const float* alpha_px;   // [H][W] data weights (nullable: alpha)
     const uint8_t* wh;
@@ -137,6 +140,7 @@ struct AdjArgs {
 struct LinAdjArgs {
     int H, W, L;
     const uint8_t* cost;
+    const uint16_t* cost16;
     const float* costf;
     const float* alpha_px;
     float alpha, h;
@@ -180,8 +184,8 @@ int penalty_taps(int omega, int L, const dm_params& p, int32_t* row);
 cudaError_t launch_census_edges(const uint8_t* left, const uint8_t* right, int H, int W, int win,
                                 int T, int w_hi, int w_lo, uint32_t* census, uint8_t* wh,
                                 uint8_t* wv, cudaStream_t s);
-cudaError_t launch_cost(const uint32_t* census, int H, int W, int L, int maxc, uint8_t* cost,
-                        cudaStream_t s);
+cudaError_t launch_cost(const uint32_t* census, int H, int W, int L, int maxc, void* cost,
+                        int cost_bytes, cudaStream_t s);
 
 // dmm.cu
 cudaError_t launch_dmm_pass(const DmmArgs& a, int lpt, int radius, cudaStream_t s);
@@ -192,10 +196,13 @@ cudaError_t launch_dmm16_pass(const Dmm16Args& a, int np, int radius, int delta_
 cudaError_t launch_validate_edges(const uint8_t* wh, const uint8_t* wv, int H, int W,
                                   const int32_t* taps, int32_t* err, cudaStream_t s);
 cudaError_t launch_duals_to_i32(const int32_t* base, const void* delta, int delta_bytes,
-                                const uint8_t* cost, long long n_px, int L, int32_t* out,
-                                cudaStream_t s);
-cudaError_t launch_theta_h_init(const uint8_t* cost, int32_t* base, void* delta, int delta_bytes,
-                                long long n_px, int L, cudaStream_t s);
+                                const void* cost, int cost_bytes, long long n_px, int L,
+                                int32_t* out, cudaStream_t s);
+cudaError_t launch_theta_h_init(const void* cost, int cost_bytes, int32_t* base, void* delta,
+                                int delta_bytes, long long n_px, int L, cudaStream_t s);
+cudaError_t launch_theta_h_from_i32(const int32_t* lam_v, const void* cost, int cost_bytes,
+                                    int32_t* base, void* delta, int delta_bytes, long long n_px,
+                                    int L, int32_t* err, cudaStream_t s);
 
 // pd.cu
 cudaError_t launch_init_u_from_labels(const uint16_t* labels, float* u, int n, cudaStream_t s);

@@ -24,8 +24,9 @@
 //     omega r(d) < omega C can beat the cap min(a) + omega C.  Neighbouring
 //     labels in other lanes are fetched with shuffles, the cap with one
 //     warp-wide REDUX min.
-//   * All arithmetic is int32 without normalisation; with costs <= 255 and
-//     chains of at most 2^16 nodes no value approaches the int32 range.
+//   * All arithmetic is int32 without normalisation; the host admits a cost
+//     volume only if (max cost + 4 omega C) times the chain length stays below
+//     2^30, so no value approaches the int32 range.
 
 #include "dm_internal.cuh"
 
@@ -34,6 +35,12 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr unsigned kFull = 0xffffffffu;
+
+// cost sample i of the uint8 or uint16 volume
+__device__ __forceinline__ int cost_of(const DmmArgs& A, size_t i)
+{
+    return A.cost16 != nullptr ? (int)__ldg(A.cost16 + i) : (int)__ldg(A.cost + i);
+}
 
 // value of label index (lane * LPT + j + off) for a compile-time off in [-R, LPT-1+R]
 template <int LPT, int OFF>
@@ -113,7 +120,7 @@ __device__ __forceinline__ void load_theta(const DmmArgs& A, const Chain& ch, in
         int v = kInf;
         if (l < ch.L) {
             v = __ldg(A.lam_in + base + j);
-            if (ch.which == 0) v += (int)__ldg(A.cost + base + j);
+            if (ch.which == 0) v += cost_of(A, base + j);
         }
         th[j] = v;
     }
@@ -283,7 +290,7 @@ __global__ void __launch_bounds__(kWarps * 32) dmm_pass_kernel(const DmmArgs A)
             if (l < A.L) {
                 const int inl = __ldg(A.lam_in + base + j);
                 int out = fk[j] + bk[j];                  // lambda_out = theta + F + B - lam_in
-                if (A.which == 0) out += (int)__ldg(A.cost + base + j);
+                if (A.which == 0) out += cost_of(A, base + j);
                 A.lam_out[base + j] = out;
                 const int nu = out + inl;                 // lambda_h + lambda_v
                 if (nu < best) {

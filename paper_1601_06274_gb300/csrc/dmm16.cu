@@ -122,6 +122,7 @@ __device__ __forceinline__ void msg16(uint32_t (&a)[NP], uint32_t (&out)[NP], in
 
 struct Ctx16 {
     int which, H, W, L, n, c, KP2;  // KP2: packed registers per stored message (32 * NP)
+    bool c16;                       // uint16 cost volume
     __device__ __forceinline__ int pix(int k) const { return which == 0 ? c * W + k : k * W + c; }
 };
 
@@ -165,7 +166,7 @@ constexpr int kL0 = 3;   // levels below this one are walked per warp without ba
 template <int NP, typename DT>
 struct Geo {
     static constexpr int ROW = 64 * NP * (int)sizeof(DT);  // unary row of 64 NP labels
-    static constexpr int CROW = 64 * NP;                    // cost row
+    static constexpr int CROW = 128 * NP;                   // cost row (uint8 or uint16)
     static constexpr int BLK = kBlk * ROW + 64;             // rows, 8 bases, 8 omega words
     static constexpr int NODE = ROW + CROW + 16;            // Handshake node: row, cost, base, omega
     static constexpr int MSG = 128 * NP + 16;               // packed message + offset
@@ -209,8 +210,15 @@ __device__ __forceinline__ void issue_node(const Dmm16Args& A, const Ctx16& C, i
     if (lane < 4)
         cp_bytes(slot + q * part, reinterpret_cast<const uint8_t*>(A.delta_in) + (size_t)pix * rowd + q * part,
                  part);
-    else if (lane < 8)
-        cp_bytes(slot + G::ROW + q * (C.L >> 2), A.cost + (size_t)pix * C.L + q * (C.L >> 2), C.L >> 2);
+    else if (lane < 8) {
+        if (A.cost16 != nullptr)
+            cp_bytes(slot + G::ROW + q * (C.L >> 1),
+                     reinterpret_cast<const uint8_t*>(A.cost16 + (size_t)pix * C.L) + q * (C.L >> 1),
+                     C.L >> 1);
+        else
+            cp_bytes(slot + G::ROW + q * (C.L >> 2), A.cost + (size_t)pix * C.L + q * (C.L >> 2),
+                     C.L >> 2);
+    }
     else if (lane == 8)
         cp_async<4>(slot + G::ROW + G::CROW, A.base_in + pix);
     else if (lane == 9 && edge >= 0)
@@ -261,10 +269,16 @@ __device__ __forceinline__ void read_row(const uint8_t* row, int lane, bool pad,
     }
 }
 
-// cost bytes of this lane's labels as packed 16-bit pairs
+// costs of this lane's labels as packed 16-bit pairs (a staged uint8 or uint16 row)
 template <int NP>
-__device__ __forceinline__ void read_cost(const uint8_t* crow, int lane, uint32_t (&cv)[NP])
+__device__ __forceinline__ void read_cost(const uint8_t* crow, int lane, bool c16, uint32_t (&cv)[NP])
 {
+    if (c16) {
+        const uint32_t* p = reinterpret_cast<const uint32_t*>(crow + lane * 4 * NP);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) cv[q] = p[q];
+        return;
+    }
     uint32_t w[(2 * NP + 3) / 4];
     const uint8_t* p = crow + lane * 2 * NP;
     if constexpr (NP == 1) w[0] = *reinterpret_cast<const uint16_t*>(p);
@@ -506,7 +520,7 @@ __device__ __forceinline__ Node<NP> read_node(const uint8_t* slot, const Ctx16& 
     using G = Geo<NP, DT>;
     Node<NP> v;
     read_row<NP, DT>(slot, lane, pad, v.th);
-    read_cost<NP>(slot + G::ROW, lane, v.cv);
+    read_cost<NP>(slot + G::ROW, lane, C.c16, v.cv);
     v.base = *reinterpret_cast<const int*>(slot + G::ROW + G::CROW);
     const uint32_t w = *reinterpret_cast<const uint32_t*>(slot + G::ROW + G::CROW + 4);
     v.om = edge >= 0 ? (int)((w >> (8 * (C.pix(edge) & 3))) & 0xffu) : 0;
@@ -643,6 +657,7 @@ __global__ void __launch_bounds__(kWarps * 32, 3) dmm16_kernel(const Dmm16Args A
     C.n = A.which == 0 ? A.W : A.H;
     C.c = blockIdx.x;
     C.KP2 = 32 * NP;
+    C.c16 = A.cost16 != nullptr;
     const int n = C.n;
     const bool pad = PAD && (lane * 2 * NP >= A.L);
     long long lb_acc = 0;
@@ -881,9 +896,15 @@ __global__ void validate_edges_kernel(const uint8_t* __restrict__ wh, const uint
     if (bad) atomicOr(err, kDevErrBadOmega);
 }
 
+__device__ __forceinline__ int cost_at(const void* cost, int cost_bytes, long long t)
+{
+    return cost_bytes == 2 ? (int)static_cast<const uint16_t*>(cost)[t]
+                           : (int)static_cast<const uint8_t*>(cost)[t];
+}
+
 // out = base + delta - (cost if given): lambda_h, or lambda_v from c + lambda_v
 __global__ void duals_to_i32_kernel(const int32_t* __restrict__ base, const void* __restrict__ delta,
-                                    int delta_bytes, const uint8_t* __restrict__ cost,
+                                    int delta_bytes, const void* __restrict__ cost, int cost_bytes,
                                     long long n_px, int L, int32_t* __restrict__ out)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -891,18 +912,56 @@ __global__ void duals_to_i32_kernel(const int32_t* __restrict__ base, const void
     const long long px = t / L;
     const int d = delta_bytes == 1 ? (int)static_cast<const uint8_t*>(delta)[t]
                                    : (int)static_cast<const int16_t*>(delta)[t];
-    out[t] = base[px] + d - (cost != nullptr ? (int)cost[t] : 0);
+    out[t] = base[px] + d - (cost != nullptr ? cost_at(cost, cost_bytes, t) : 0);
 }
 
 // cold start of the 16-bit path: the horizontal unary c + lambda_v with lambda_v = 0
-__global__ void theta_h_init_kernel(const uint8_t* __restrict__ cost, int32_t* __restrict__ base,
-                                    void* __restrict__ delta, int delta_bytes, long long n_px, int L)
+__global__ void theta_h_init_kernel(const void* __restrict__ cost, int cost_bytes,
+                                    int32_t* __restrict__ base, void* __restrict__ delta,
+                                    int delta_bytes, long long n_px, int L)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n_px) base[t] = 0;
     if (t >= n_px * L) return;
-    if (delta_bytes == 1) static_cast<uint8_t*>(delta)[t] = cost[t];
-    else static_cast<int16_t*>(delta)[t] = (int16_t)cost[t];
+    const int c = cost_at(cost, cost_bytes, t);
+    if (delta_bytes == 1) static_cast<uint8_t*>(delta)[t] = (uint8_t)c;
+    else static_cast<int16_t*>(delta)[t] = (int16_t)c;
+}
+
+// warm start of the 16-bit path: the horizontal unary c + lambda_v for a new
+// cost volume c and int32 lambda_v, one warp per pixel: base = the minimum over
+// the labels rounded down to even (the kernel's halving commutes only with
+// even shifts), deltas above it; a span the deltas cannot hold sets
+// kDevErrRange
+__global__ void theta_h_from_i32_kernel(const int32_t* __restrict__ lam_v,
+                                        const void* __restrict__ cost, int cost_bytes,
+                                        int32_t* __restrict__ base, void* __restrict__ delta,
+                                        int delta_bytes, long long n_px, int L,
+                                        int32_t* __restrict__ err)
+{
+    const long long px = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (px >= n_px) return;
+    const long long row = px * L;
+    int mn = INT_MAX, mx = INT_MIN;
+    for (int l = lane; l < L; l += 32) {
+        const int v = lam_v[row + l] + cost_at(cost, cost_bytes, row + l);
+        mn = min(mn, v);
+        mx = max(mx, v);
+    }
+    mn = __reduce_min_sync(0xffffffffu, mn) & ~1;
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    const int cap = delta_bytes == 1 ? 255 : 16000;
+    if (mx - mn > cap) {
+        if (lane == 0) atomicOr(err, kDevErrRange);
+        return;
+    }
+    for (int l = lane; l < L; l += 32) {
+        const int d = lam_v[row + l] + cost_at(cost, cost_bytes, row + l) - mn;
+        if (delta_bytes == 1) static_cast<uint8_t*>(delta)[row + l] = (uint8_t)d;
+        else static_cast<int16_t*>(delta)[row + l] = (int16_t)d;
+    }
+    if (lane == 0) base[px] = mn;
 }
 
 }  // namespace
@@ -923,21 +982,31 @@ cudaError_t launch_validate_edges(const uint8_t* wh, const uint8_t* wv, int H, i
 }
 
 cudaError_t launch_duals_to_i32(const int32_t* base, const void* delta, int delta_bytes,
-                                const uint8_t* cost, long long n_px, int L, int32_t* out,
-                                cudaStream_t s)
+                                const void* cost, int cost_bytes, long long n_px, int L,
+                                int32_t* out, cudaStream_t s)
 {
     const long long total = n_px * L;
-    duals_to_i32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(base, delta, delta_bytes,
-                                                                          cost, n_px, L, out);
+    duals_to_i32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        base, delta, delta_bytes, cost, cost_bytes, n_px, L, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_theta_h_init(const uint8_t* cost, int32_t* base, void* delta, int delta_bytes,
-                                long long n_px, int L, cudaStream_t s)
+cudaError_t launch_theta_h_init(const void* cost, int cost_bytes, int32_t* base, void* delta,
+                                int delta_bytes, long long n_px, int L, cudaStream_t s)
 {
     const long long total = n_px * L;
-    theta_h_init_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(cost, base, delta,
-                                                                          delta_bytes, n_px, L);
+    theta_h_init_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        cost, cost_bytes, base, delta, delta_bytes, n_px, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_theta_h_from_i32(const int32_t* lam_v, const void* cost, int cost_bytes,
+                                    int32_t* base, void* delta, int delta_bytes, long long n_px,
+                                    int L, int32_t* err, cudaStream_t s)
+{
+    const long long threads = n_px * 32;
+    theta_h_from_i32_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        lam_v, cost, cost_bytes, base, delta, delta_bytes, n_px, L, err);
     return cudaGetLastError();
 }
 

@@ -23,9 +23,20 @@ namespace {
 
 constexpr int kTX = 32, kTY = 8;
 
-__device__ __forceinline__ float cost_sample(const uint8_t* c8, const float* cf, size_t i)
+// the cost samples: float32, uint16 or uint8 (the first that is set)
+struct CostSrc {
+    const uint8_t* c8;
+    const uint16_t* c16;
+    const float* cf;
+};
+
+__device__ __forceinline__ CostSrc cost_src(const PdArgs& A) { return {A.cost, A.cost16, A.costf}; }
+
+__device__ __forceinline__ float cost_sample(const CostSrc& c, size_t i)
 {
-    return cf != nullptr ? __ldg(cf + i) : (float)__ldg(c8 + i);
+    if (c.cf != nullptr) return __ldg(c.cf + i);
+    if (c.c16 != nullptr) return (float)__ldg(c.c16 + i);
+    return (float)__ldg(c.c8 + i);
 }
 
 // The forward iteration and its reverse (below) recompute the same quantities
@@ -34,15 +45,15 @@ __device__ __forceinline__ float cost_sample(const uint8_t* c8, const float* cf,
 
 // D_i(x): linear interpolation of the cost samples of pixel px with the argument
 // clamped to [0, L-1]
-__device__ __forceinline__ float interp(const uint8_t* c8, const float* cf, int L, size_t px, float x)
+__device__ __forceinline__ float interp(const CostSrc& c, int L, size_t px, float x)
 {
     x = fminf(fmaxf(x, 0.0f), (float)(L - 1));
     int k = (int)floorf(x);
     if (k > L - 2) k = L - 2;
     if (k < 0) k = 0;
     const float t = __fsub_rn(x, (float)k);
-    const float c0 = cost_sample(c8, cf, px * L + k);
-    const float c1 = cost_sample(c8, cf, px * L + k + 1);
+    const float c0 = cost_sample(c, px * L + k);
+    const float c1 = cost_sample(c, px * L + k + 1);
     return __fmaf_rn(t, __fsub_rn(c1, c0), c0);
 }
 
@@ -57,13 +68,13 @@ struct LinPx {
     float dm, d0, dp, s1, s2;
 };
 
-__device__ __forceinline__ LinPx lin_px(const uint8_t* c8, const float* cf, int L, size_t px,
-                                        float al, float u0, float h)
+__device__ __forceinline__ LinPx lin_px(const CostSrc& c, int L, size_t px, float al, float u0,
+                                        float h)
 {
     LinPx r;
-    r.d0 = interp(c8, cf, L, px, u0);
-    r.dm = interp(c8, cf, L, px, __fsub_rn(u0, h));
-    r.dp = interp(c8, cf, L, px, __fadd_rn(u0, h));
+    r.d0 = interp(c, L, px, u0);
+    r.dm = interp(c, L, px, __fsub_rn(u0, h));
+    r.dp = interp(c, L, px, __fadd_rn(u0, h));
     r.s1 = __fdiv_rn(__fmul_rn(al, __fsub_rn(r.d0, r.dm)), h);
     r.s2 = __fdiv_rn(__fmul_rn(al, __fsub_rn(r.dp, r.d0)), h);
     return r;
@@ -90,7 +101,7 @@ __global__ void linearise_kernel(const PdArgs A)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float u0 = A.u[i];
-    const LinPx l = lin_px(A.cost, A.costf, A.L, i, alpha_of(A.alpha_px, A.alpha, i), u0, A.h);
+    const LinPx l = lin_px(cost_src(A), A.L, i, alpha_of(A.alpha_px, A.alpha, i), u0, A.h);
     float s1 = l.s1, s2 = l.s2;
     if (s2 < s1) {
         s1 = 0.5f * __fadd_rn(s1, s2);
@@ -257,7 +268,7 @@ __global__ void energy_kernel(const PdArgs A, double eps, double delta, double C
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int x = i % A.W, y = i / A.W;
         const float* u = A.u;
-        acc += (double)alpha_of(A.alpha_px, A.alpha, i) * (double)interp(A.cost, A.costf, A.L, i, u[i]);
+        acc += (double)alpha_of(A.alpha_px, A.alpha, i) * (double)interp(cost_src(A), A.L, i, u[i]);
         if (x + 1 < A.W)
             acc += (double)A.lambda_r * A.wh[i] * r_dc((double)u[i] - (double)u[i + 1], eps, delta, C);
         if (y + 1 < A.H)
@@ -403,13 +414,12 @@ __global__ void __launch_bounds__(kTX * kTY) pd_adjoint_kernel(const AdjArgs A)
 }
 
 // d D_i(x) / dx of the clamped interpolation (zero outside [0, L-1])
-__device__ __forceinline__ float interp_dx(const uint8_t* c8, const float* cf, int L, size_t px,
-                                           float x)
+__device__ __forceinline__ float interp_dx(const CostSrc& c, int L, size_t px, float x)
 {
     if (x < 0.0f || x > (float)(L - 1)) return 0.0f;
     int k = (int)floorf(x);
     if (k > L - 2) k = L - 2;
-    return cost_sample(c8, cf, px * L + k + 1) - cost_sample(c8, cf, px * L + k);
+    return cost_sample(c, px * L + k + 1) - cost_sample(c, px * L + k);
 }
 
 // g += w * d D_i(x) / d c_i
@@ -434,7 +444,8 @@ __global__ void lin_adjoint_kernel(const LinAdjArgs A)
     if (i >= n) return;
     const float u0 = A.u0[i], h = A.h;
     const float al = alpha_of(A.alpha_px, A.alpha, i);
-    const LinPx l = lin_px(A.cost, A.costf, A.L, i, al, u0, h);
+    const CostSrc cs{A.cost, A.cost16, A.costf};
+    const LinPx l = lin_px(cs, A.L, i, al, u0, h);
     float b1 = A.gs1[i], b2 = A.gs2[i];
     if (l.s2 < l.s1) b1 = b2 = 0.5f * (b1 + b2);
     const float um = __fsub_rn(u0, h), up = __fadd_rn(u0, h);
@@ -445,9 +456,9 @@ __global__ void lin_adjoint_kernel(const LinAdjArgs A)
         interp_dc(g, A.L, um, -al / h * b1);
         interp_dc(g, A.L, up, al / h * b2);
     }
-    const float x0 = interp_dx(A.cost, A.costf, A.L, i, u0);
-    const float xm = interp_dx(A.cost, A.costf, A.L, i, um);
-    const float xp = interp_dx(A.cost, A.costf, A.L, i, up);
+    const float x0 = interp_dx(cs, A.L, i, u0);
+    const float xm = interp_dx(cs, A.L, i, um);
+    const float xp = interp_dx(cs, A.L, i, up);
     A.ub[i] += A.gu0[i] + al / h * (b1 * (x0 - xm) + b2 * (xp - x0));
     A.gu0[i] = 0.0f;
     A.gs1[i] = 0.0f;
@@ -470,15 +481,17 @@ __global__ void lin_jvp_kernel(const JvpArgs J)
     const float u0 = A.u[i], du0 = J.du[i], h = A.h;
     const float al = alpha_of(A.alpha_px, A.alpha, i);
     const float dal = J.dalpha != nullptr ? J.dalpha[i] : 0.0f;
-    const LinPx l = lin_px(A.cost, A.costf, A.L, i, al, u0, h);
+    const CostSrc cs = cost_src(A);
+    const LinPx l = lin_px(cs, A.L, i, al, u0, h);
     const float um = __fsub_rn(u0, h), up = __fadd_rn(u0, h);
-    float dd0 = interp_dx(A.cost, A.costf, A.L, i, u0) * du0;
-    float ddm = interp_dx(A.cost, A.costf, A.L, i, um) * du0;
-    float ddp = interp_dx(A.cost, A.costf, A.L, i, up) * du0;
+    float dd0 = interp_dx(cs, A.L, i, u0) * du0;
+    float ddm = interp_dx(cs, A.L, i, um) * du0;
+    float ddp = interp_dx(cs, A.L, i, up) * du0;
     if (J.dcost != nullptr) {
-        dd0 += interp(nullptr, J.dcost, A.L, i, u0);
-        ddm += interp(nullptr, J.dcost, A.L, i, um);
-        ddp += interp(nullptr, J.dcost, A.L, i, up);
+        const CostSrc dc{nullptr, nullptr, J.dcost};
+        dd0 += interp(dc, A.L, i, u0);
+        ddm += interp(dc, A.L, i, um);
+        ddp += interp(dc, A.L, i, up);
     }
     float s1 = l.s1, s2 = l.s2;
     float ds1 = (dal * (l.d0 - l.dm) + al * (dd0 - ddm)) / h;

@@ -34,7 +34,8 @@ class DmParams(ctypes.Structure):
                 ("C", ctypes.c_double), ("lambda_r", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("tau", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("h", ctypes.c_double), ("warps", ctypes.c_int32),
-                ("dmm_path", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("dmm_path", ctypes.c_int32), ("cost_bytes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 _lib = None
@@ -73,9 +74,13 @@ def lib() -> ctypes.CDLL:
             "dm_energy": [_vp, ctypes.POINTER(ctypes.c_double)],
             "dm_sync": [_vp],
             "dm_launch_count": [_vp, ctypes.POINTER(ctypes.c_uint64)],
+            "dm_get_path": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
             "dm_discrete_pass_noalloc": [_i, _i, _i, ctypes.POINTER(DmParams), _i, _vp, _vp,
                                          _vp, _vp, _vp, _vp],
             "dm_set_cost_volume_f32": [_vp, _vp, _vp, _vp],
+            "dm_set_cost_volume_u16": [_vp, _vp, _vp, _vp, _i],
+            "dm_cost_volume_warm": [_vp, _vp, _vp],
+            "dm_solve_next": [_vp, _vp, _vp, _i, _i, _vp],
             "dm_set_data_weights": [_vp, _vp],
             "dm_set_lambda_r": [_vp, ctypes.c_double],
             "dm_tape_bytes": [_vp, _i, _i, ctypes.POINTER(ctypes.c_size_t)],
@@ -172,6 +177,28 @@ class Context:
         _ck(lib().dm_set_cost_volume(self._h, self._c.data_ptr(), self._wh.data_ptr(),
                                      self._wv.data_ptr()), "dm_set_cost_volume")
 
+    def set_cost_volume_u16(self, cost, wh, wv, cost_max: int):
+        torch = self._torch
+        c = torch.as_tensor(np.ascontiguousarray(cost).view(np.int16)) \
+            if isinstance(cost, np.ndarray) else cost
+        self._c = c.to(self.device).contiguous()
+        self._wh, self._wv = self._dev_u8(wh), self._dev_u8(wv)
+        _ck(lib().dm_set_cost_volume_u16(self._h, self._c.data_ptr(), self._wh.data_ptr(),
+                                         self._wv.data_ptr(), int(cost_max)),
+            "dm_set_cost_volume_u16")
+
+    def cost_volume_warm(self, left, right):
+        self._left, self._right = self._dev_u8(left), self._dev_u8(right)
+        _ck(lib().dm_cost_volume_warm(self._h, self._left.data_ptr(), self._right.data_ptr()),
+            "dm_cost_volume_warm")
+
+    def solve_next(self, left, right, dmm_iters: int, pd_iters: int, out=None):
+        self._left, self._right = self._dev_u8(left), self._dev_u8(right)
+        out = out if out is not None else self._empty((self.H, self.W), self._torch.float32)
+        _ck(lib().dm_solve_next(self._h, self._left.data_ptr(), self._right.data_ptr(), dmm_iters,
+                                pd_iters, out.data_ptr()), "dm_solve_next")
+        return out
+
     def reset_duals(self):
         _ck(lib().dm_reset_duals(self._h), "dm_reset_duals")
 
@@ -226,7 +253,10 @@ class Context:
         return lh, lv
 
     def cost(self):
-        c = self._empty((self.H, self.W, self.L), self._torch.uint8)
+        """(cost volume, wh, wv); the cost is int16 holding uint16 samples when
+        params.cost_bytes = 2 (numpy: .view(np.uint16))."""
+        dt = self._torch.int16 if self.params.cost_bytes == 2 else self._torch.uint8
+        c = self._empty((self.H, self.W, self.L), dt)
         wh = self._empty((self.H, self.W), self._torch.uint8)
         wv = self._empty((self.H, self.W), self._torch.uint8)
         _ck(lib().dm_get_cost_volume(self._h, c.data_ptr(), wh.data_ptr(), wv.data_ptr()),
@@ -314,6 +344,12 @@ class Context:
                                 du.data_ptr(), scratch.data_ptr(), n.value), "dm_refine_jvp")
         self._jvp_keep = (keep, scratch)
         return du
+
+    def path(self):
+        """(Dual MM kernel: 16 or 32, bytes per dual delta)"""
+        k, d = ctypes.c_int(), ctypes.c_int()
+        _ck(lib().dm_get_path(self._h, ctypes.byref(k), ctypes.byref(d)), "dm_get_path")
+        return k.value, d.value
 
     def launch_count(self) -> int:
         n = ctypes.c_uint64()

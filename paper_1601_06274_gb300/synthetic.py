@@ -22,6 +22,10 @@ The paper's own inputs (KITTI-like driving stereo, Middlebury, a live 640x480
 camera) are not available here; these pairs stand in for them with the same
 shapes, label counts and image statistics (band-limited texture, piecewise
 planar disparity, occlusions, sensor noise).
+
+Sequences (the streaming workload): one band-limited scene texture, wider than
+a frame, pans one pixel per frame; the planes drift by a small random walk;
+each frame's right view is made as above with its own noise.
 """
 
 from __future__ import annotations
@@ -68,35 +72,42 @@ def _texture(rng: np.random.Generator, H: int, W: int) -> np.ndarray:
     return ((b - lo) * 255 // (hi - lo)).astype(np.uint8)
 
 
-def _planes(rng: np.random.Generator, H: int, W: int, L: int, P: int) -> np.ndarray:
-    """Piecewise-planar disparity: one slanted plane per Voronoi cell."""
+def _plane_params(rng: np.random.Generator, H: int, W: int, L: int, P: int) -> dict:
+    """P slanted planes: seed points, the value at each seed in [0, L-1], gentle slopes."""
     sy = rng.integers(0, H, size=P)
     sx = rng.integers(0, W, size=P)
-    # plane parameters: value at the seed in [0, L-1], gentle slopes
     c_at_seed = rng.uniform(0.0, L - 1.0, size=P)
     slope = (L - 1.0) / max(W, H)
     a = rng.uniform(-0.5 * slope, 0.5 * slope, size=P)
     b = rng.uniform(-0.5 * slope, 0.5 * slope, size=P)
+    return dict(sy=sy, sx=sx, c=c_at_seed, a=a, b=b)
+
+
+def _render_planes(pp: dict, H: int, W: int, L: int) -> np.ndarray:
+    """Piecewise-planar disparity: one slanted plane per Voronoi cell of the seeds."""
+    sy, sx = pp["sy"], pp["sx"]
     yy, xx = np.mgrid[0:H, 0:W]
     best = np.full((H, W), np.iinfo(np.int64).max, dtype=np.int64)
     cell = np.zeros((H, W), dtype=np.int64)
-    for p in range(P):
+    for p in range(len(sy)):
         d2 = (yy - sy[p]).astype(np.int64) ** 2 + (xx - sx[p]).astype(np.int64) ** 2
         closer = d2 < best
         best[closer] = d2[closer]
         cell[closer] = p
     dx = xx - sx[cell]
     dy = yy - sy[cell]
-    d = c_at_seed[cell] + a[cell] * dx + b[cell] * dy
+    d = pp["c"][cell] + pp["a"][cell] * dx + pp["b"][cell] * dy
     return np.clip(d, 0.0, L - 1.0)
 
 
-def make_pair(H: int, W: int, L: int, *, planes: int = 4, noise_sigma: float = 2.0,
-              min_occluded: float = 0.0, seed: int = 0) -> StereoPair:
-    """One synthetic rectified stereo pair; see the module docstring."""
-    rng = np.random.default_rng(seed)
-    left = _texture(rng, H, W)
-    gt = _planes(rng, H, W, L, planes)
+def _planes(rng: np.random.Generator, H: int, W: int, L: int, P: int) -> np.ndarray:
+    return _render_planes(_plane_params(rng, H, W, L, P), H, W, L)
+
+
+def _right_image(rng: np.random.Generator, left: np.ndarray, gt: np.ndarray, noise_sigma: float,
+                 min_occluded: float):
+    """The right view of `left` under disparity `gt` (see the module docstring)."""
+    H, W = left.shape
     d_int = np.rint(gt).astype(np.int64)
     right = np.zeros((H, W), dtype=np.int64)
     zbuf = np.full((H, W), -1, dtype=np.int64)
@@ -124,8 +135,37 @@ def make_pair(H: int, W: int, L: int, *, planes: int = 4, noise_sigma: float = 2
             occluded |= disc
     if noise_sigma > 0:
         right = right + np.rint(rng.normal(0.0, noise_sigma, size=(H, W))).astype(np.int64)
-    right = np.clip(right, 0, 255).astype(np.uint8)
+    return np.clip(right, 0, 255).astype(np.uint8), occluded
+
+
+def make_pair(H: int, W: int, L: int, *, planes: int = 4, noise_sigma: float = 2.0,
+              min_occluded: float = 0.0, seed: int = 0) -> StereoPair:
+    """One synthetic rectified stereo pair; see the module docstring."""
+    rng = np.random.default_rng(seed)
+    left = _texture(rng, H, W)
+    gt = _planes(rng, H, W, L, planes)
+    right, occluded = _right_image(rng, left, gt, noise_sigma, min_occluded)
     return StereoPair(left=left, right=right, gt=gt, occluded=occluded, seed=seed)
+
+
+def make_sequence(H: int, W: int, L: int, frames: int, *, planes: int = 12,
+                  noise_sigma: float = 3.0, drift: float = 0.25, pan: int = 1, seed: int = 0):
+    """A sequence of pairs: the scene texture pans `pan` pixels per frame and the
+    ground-truth planes drift (a random walk of `drift` labels in each plane's
+    offset and drift / max(H, W) in its slopes per frame).  Yields StereoPair."""
+    rng = np.random.default_rng(seed)
+    scene = _texture(rng, H, W + pan * frames)
+    pp = _plane_params(rng, H, W, L, planes)
+    for f in range(frames):
+        if f > 0:
+            P = len(pp["c"])
+            pp = dict(pp, c=np.clip(pp["c"] + rng.uniform(-drift, drift, size=P), 0.0, L - 1.0),
+                      a=pp["a"] + rng.uniform(-drift, drift, size=P) / max(H, W),
+                      b=pp["b"] + rng.uniform(-drift, drift, size=P) / max(H, W))
+        left = np.ascontiguousarray(scene[:, pan * f:pan * f + W])
+        gt = _render_planes(pp, H, W, L)
+        right, occluded = _right_image(np.random.default_rng((seed, f)), left, gt, noise_sigma, 0.0)
+        yield StereoPair(left=left, right=right, gt=gt, occluded=occluded, seed=seed)
 
 
 # ---------------------------------------------------------------------------
@@ -138,6 +178,9 @@ SMALL = dict(H=48, W=64, L=16, planes=4, noise_sigma=2.0, min_occluded=0.0,
 #: KITTI-shaped 1242x375 pair, 128 labels, 12 planes, 5% occluded, sigma_n = 3
 KITTI = dict(H=375, W=1242, L=128, planes=12, noise_sigma=3.0, min_occluded=0.05,
              dmm_iters=10, pd_iters=100)
+#: streaming: 60 frames of 1920x1080 with 256 labels (uint16 cost volume), drifting planes
+STREAM = dict(H=1080, W=1920, L=256, planes=12, noise_sigma=3.0, frames=60, drift=0.25,
+              dmm_iters=10, pd_iters=100)
 
 
 def make_workload(spec: dict, seed: int = 0) -> StereoPair:
