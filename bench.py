@@ -38,10 +38,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="kitti", choices=["kitti", "diff", "stream"],
+    ap.add_argument("--workload", default="kitti", choices=["kitti", "diff", "stream", "batch"],
                     help="kitti: the plain method on the 1242x375x128 frame (default); "
                          "diff: forward + reverse mode of 200 PD iterations at 512x256x96; "
-                         "stream: 60 warm-started frames of 1920x1080x256 (uint16 costs)")
+                         "stream: 60 warm-started frames of 1920x1080x256 (uint16 costs); "
+                         "batch: 32 pairs of mixed size and label count in one CUDA graph")
     return ap.parse_args()
 
 
@@ -468,6 +469,114 @@ def run_stream(args):
 
 
 # ---------------------------------------------------------------------------
+# Batched form: 32 pairs of mixed size and label count, one captured graph
+# ---------------------------------------------------------------------------
+
+def run_batch(args):
+    import numpy as np
+    import torch
+    from paper_1601_06274_gb300 import build, dm, synthetic as S
+    build.build()
+    dev = torch.device("cuda", 0)
+    specs = S.batch_specs(32, seed=0)
+    shapes = [(s["H"], s["W"], s["L"]) for s in specs]
+    NI, NP = specs[0]["dmm_iters"], specs[0]["pd_iters"]
+    pairs = [S.make_workload(s, seed=s["seed"]) for s in specs]
+    b = dm.Batch(shapes, device=str(dev))
+    lefts = [torch.from_numpy(p.left).to(dev) for p in pairs]
+    rights = [torch.from_numpy(p.right).to(dev) for p in pairs]
+    cache = os.path.join(tempfile.gettempdir(), "dm_batch_tune.txt")
+    t0 = time.perf_counter()
+    choice = b.tune(lefts, rights, cache)
+    tune_s = time.perf_counter() - t0
+    outs = b.outputs()
+    b.capture(lefts, rights, NI, NP, outs)
+    for _ in range(args.warmup):
+        b.replay()
+    b.sync()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = b.stream
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    launches0 = b.launch_count()
+    clk = Clocks(0)
+    for k in range(args.steps):
+        with torch.cuda.stream(st):
+            flush.fill_(k & 0xff)
+            evs[k][0].record(st)
+        b.replay()
+        with torch.cuda.stream(st):
+            evs[k][1].record(st)
+    b.sync()
+    clocks = clk.stop()
+    launches = b.launch_count() - launches0
+    tot_ms = sum(a.elapsed_time(c) for a, c in evs)
+    units = sum(H * W * L for H, W, L in shapes)
+    value = units * args.steps / (tot_ms / 1e3) / 1e6
+    # the same 32 pairs one after another through the single-pair path
+    ctxs = [dm.Context(H, W, L, device=str(dev)) for H, W, L in shapes]
+    for c, l, r in zip(ctxs, lefts, rights):
+        c.solve(l, r, NI, NP)
+    torch.cuda.synchronize()
+    sp_ms = []
+    for k in range(max(1, args.steps // 2)):
+        flush.fill_(k & 0xff)
+        a, c2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for c, l, r in zip(ctxs, lefts, rights):
+            c.solve(l, r, NI, NP)
+        c2.record()
+        torch.cuda.synchronize()
+        sp_ms.append(a.elapsed_time(c2))
+    single_ms = sum(sp_ms) / len(sp_ms)
+    # end to end: pinned host images into the captured buffers, disparities back
+    h_l = [torch.from_numpy(p.left).pin_memory() for p in pairs]
+    h_r = [torch.from_numpy(p.right).pin_memory() for p in pairs]
+    h_u = [torch.empty(o.shape, dtype=torch.float32).pin_memory() for o in outs]
+    torch.cuda.synchronize()
+    e_ms = []
+    for k in range(args.steps):
+        a, c2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            a.record(st)
+            for i in range(len(pairs)):
+                lefts[i].copy_(h_l[i], non_blocking=True)
+                rights[i].copy_(h_r[i], non_blocking=True)
+        with torch.cuda.stream(st):
+            b.replay()
+            for i in range(len(pairs)):
+                h_u[i].copy_(outs[i], non_blocking=True)
+            c2.record(st)
+        b.sync()
+        e_ms.append(a.elapsed_time(c2))
+    e2e_value = units * args.steps / (sum(e_ms) / 1e3) / 1e6
+    peak, src = hbm_peak()
+    line = {
+        "metric": "Mpixel·labels/s (discrete+continuous), 32 mixed pairs in one CUDA graph",
+        "value": round(value, 3), "unit": "Mpixel·labels/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int16x2+int32+f32", "data": "synthetic",
+        "config": {"workload": "batch-32-mixed", "pairs": len(shapes),
+                   "sizes": sorted({f"{W}x{H}" for H, W, _ in shapes}),
+                   "labels": sorted({L for _, _, L in shapes}),
+                   "pixel_labels": units, "dmm_iters": NI, "pd_iters": NP,
+                   "l2": "flushed between steps (256 MB write, outside the timed events)"},
+        "tuning": {"dmm_ctas_per_sm": choice[0], "pd_tile": f"{choice[1]}x{choice[2]}",
+                   "pd_ctas_per_sm": choice[3], "group_budget_mb": choice[4],
+                   "tune_seconds": round(tune_s, 2)},
+        "single_pair_path_ms": round(single_ms, 4),
+        "speedup_over_single_pair_path": round(single_ms / (tot_ms / args.steps), 3),
+        "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": round(e2e_value, 3), "unit": "Mpixel·labels/s",
+                "h2d_bytes_per_step": sum(2 * H * W for H, W, _ in shapes),
+                "d2h_bytes_per_step": sum(4 * H * W for H, W, _ in shapes)},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -481,6 +590,9 @@ def main():
         return
     if args.workload == "stream":
         run_stream(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
         return
     import numpy as np
     import torch

@@ -270,6 +270,65 @@ DM_API int dm_refine_jvp(dm_ctx* ctx, int iters, const float* d_u0, const float*
                          const float* d_dcost, const float* d_dalpha, double dlambda, float* d_du,
                          void* d_scratch, size_t scratch_bytes);
 
+/* ---- Batched form ---------------------------------------------------------
+ * n stereo pairs of mixed sizes and label counts solved together: every pair
+ * has its own context (same parameters) on a slice of one workspace, and the
+ * Dual MM passes and primal-dual iterations run as persistent kernels over all
+ * pairs (one launch per label class and pass, one per iteration).  The batch
+ * runs on a stream of its own (dm_batch_set_stream; a non-default stream is
+ * needed for capture).  Results per pair are read through dm_batch_context
+ * and the single-pair getters.  The paper solves one pair at a time.
+ */
+typedef struct dm_batch dm_batch;
+
+/* H, W, L: arrays of n sizes (each as in dm_create). */
+DM_API int dm_batch_create(int n, const int* H, const int* W, const int* L, const dm_params* p,
+                           dm_batch** out);
+DM_API int dm_batch_destroy(dm_batch* b);
+DM_API int dm_batch_workspace_bytes(const dm_batch* b, size_t* bytes);
+DM_API int dm_batch_bind_workspace(dm_batch* b, void* d_workspace, size_t bytes);
+DM_API int dm_batch_set_stream(dm_batch* b, void* stream);
+/* The context of pair i (owned by the batch; do not destroy or rebind it). */
+DM_API int dm_batch_context(dm_batch* b, int i, dm_ctx** out);
+
+/* Solve every pair: cost volume, dmm_iters (1..256) Dual MM iterations,
+ * pd_iters primal-dual iterations; d_left, d_right: n device image pointers
+ * (host array); d_u: n device outputs (host array, entries nullable; NULL for
+ * none).  Asynchronous. */
+DM_API int dm_batch_solve(dm_batch* b, const uint8_t* const* d_left, const uint8_t* const* d_right,
+                          int dmm_iters, int pd_iters, float* const* d_u);
+
+/* Record one dm_batch_solve with these arguments into a CUDA graph owned by the
+ * batch (nothing runs); dm_batch_replay launches it.  The graph keeps the
+ * pointers: new inputs are written into the same image buffers between
+ * replays.  Changing the stream, workspace or tuning drops the graph. */
+DM_API int dm_batch_capture(dm_batch* b, const uint8_t* const* d_left,
+                            const uint8_t* const* d_right, int dmm_iters, int pd_iters,
+                            float* const* d_u);
+DM_API int dm_batch_replay(dm_batch* b);
+
+/* Synchronise the stream and report a device-side error of any pair. */
+DM_API int dm_batch_sync(dm_batch* b);
+
+/* Launch shapes: choice[5] = {CTAs per SM of the persistent Dual MM kernels
+ * (1-3), primal-dual tile width, tile height (32x8, 32x4, 32x16, 64x4, 64x8,
+ * 16x16), CTAs per SM of the persistent primal-dual kernel (1-64), group
+ * budget in MB: consecutive pairs whose Dual MM working set (duals and costs)
+ * fits it are solved together, both stages, before the next group (0: one
+ * group)}.
+ * dm_batch_tune times every candidate on these inputs (it runs the cost volumes
+ * and one iteration of both stages first; synchronous) and keeps the fastest;
+ * with cache_path (nullable) it first looks for a line for this GPU, these
+ * shapes and this penalty, and appends its result.  Results do not depend on
+ * the choice. */
+DM_API int dm_batch_tune(dm_batch* b, const uint8_t* const* d_left, const uint8_t* const* d_right,
+                         const char* cache_path, int* choice);
+DM_API int dm_batch_set_tuning(dm_batch* b, const int* choice);
+DM_API int dm_batch_get_tuning(const dm_batch* b, int* choice);
+
+/* Kernels enqueued for the batch (a replay counts the graph's kernels). */
+DM_API int dm_batch_launch_count(const dm_batch* b, uint64_t* count);
+
 /* Allocation-free variant of dm_discrete_pass.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
  * (a fixed memory budget decided at start-up, a real-time or embedded

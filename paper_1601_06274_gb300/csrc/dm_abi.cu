@@ -9,43 +9,7 @@
 
 #include "dm_internal.cuh"
 
-struct dm_ctx {
-    int H = 0, W = 0, L = 0, KP = 0, lpt = 0, radius = 1;
-    bool discrete_ok = true;    // w_hi and w_lo have integer penalty taps within kRMax
-    // packed 16-bit Dual MM (dmm16.cu): usable when L is a multiple of 2*np16 and
-    // every penalty cap is small; delta_bytes is chosen per cost volume
-    bool can16 = false;
-    bool use16 = false;
-    int np16 = 1;
-    int delta_bytes = 2;
-    int p2_all = 0;             // largest cap omega*C over every usable omega
-    int p2_used = 0;            // largest cap over w_hi, w_lo
-    std::vector<uint32_t> taps16;
-    dm_params p{};
-    dm::Layout lay{};
-    uint8_t* ws = nullptr;
-    size_t ws_bytes = 0;
-    cudaStream_t stream = nullptr;
-    std::vector<int32_t> taps;  // [256][kTapW]
-    bool have_cost = false;
-    bool have_labels = false;
-    bool have_u = false;
-    int u_cur = 0;              // 0: current disparity in lay.u, 1: in lay.u_new
-    int pq_cur = 0;             // 0: current p, q in lay.ph.., 1: in lay.ph2..
-    int last_iters = 0;
-    unsigned long long launches = 0;  // kernels enqueued by this context
-    bool have_weights = false;  // edge weights in the workspace
-    int cost_bytes = 1;         // storage of the cost volume: uint8 or uint16
-    int cost_max = 0;           // bound on the current cost volume's samples
-    // differentiable form: a caller's float cost volume and per-pixel data
-    // weights (borrowed, nullable) and the tape of the last checkpointed forward
-    const float* cost_f32 = nullptr;
-    const float* alpha_px = nullptr;
-    const void* tape = nullptr;
-    size_t tape_bytes = 0;
-    int tape_iters = 0, tape_ckpt = 0;
-    bool tape_valid = false;
-};
+#include "dm_ctx.cuh"
 
 namespace {
 
@@ -293,7 +257,7 @@ size_t msg16_bytes(const dm_ctx* c)
 
 size_t base_bytes(const dm_ctx* c) { return align_up((size_t)c->H * c->W * 4, 256); }
 
-int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
+dm::Dmm16Args dm16_args(dm_ctx* c, int which)
 {
     dm::Dmm16Args a{};
     uint8_t* ws = c->ws;
@@ -318,12 +282,18 @@ int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
     a.bofs = reinterpret_cast<int32_t*>(ws + c->lay.bmsg + msg16_bytes(c));
     a.taps16 = reinterpret_cast<const uint32_t*>(ws + c->lay.taps16);
     a.err = reinterpret_cast<int32_t*>(ws + c->lay.err);
-    a.labels = labels;
-    a.lb = lb;
     const int n = which == 0 ? c->W : c->H;
     int cap = 1;
     while (cap < n) cap <<= 1;
     a.seg_cap = (cap + 1 + 7) & ~7;  // keeps the second array 16-byte aligned
+    return a;
+}
+
+int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
+{
+    dm::Dmm16Args a = dm16_args(c, which);
+    a.labels = labels;
+    a.lb = lb;
     DM_CK(dm::launch_dmm16_pass(a, c->np16, c->radius, c->delta_bytes, c->stream));
     c->launches += 1;
     return DM_OK;
@@ -333,15 +303,20 @@ int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
 // cost_max: the packed 16-bit kernel needs every dual delta, at most
 // max(c) + 2 (omega C + 1), to stay below its 16-bit infinity; the int32 kernel
 // needs (max(c) + 4 omega C) times the chain length below 2^30
-int choose_path(dm_ctx* c, int cost_max, bool user_weights)
+void set_path(dm_ctx* c, int cost_max, bool user_weights)
 {
     const int p2 = user_weights ? c->p2_all : c->p2_used;
-    const long long n = (c->H > c->W ? c->H : c->W) + 1;
-    if (c->discrete_ok && ((long long)cost_max + 4LL * c->p2_all) * n >= (1LL << 30))
-        return DM_ERR_RANGE;
     c->cost_max = cost_max;
     c->use16 = c->can16 && cost_max + 2 * (p2 + 1) <= kMaxDelta16;
     c->delta_bytes = (cost_max + 2 * (p2 + 1) <= 255) ? 1 : 2;
+}
+
+int choose_path(dm_ctx* c, int cost_max, bool user_weights)
+{
+    const long long n = (c->H > c->W ? c->H : c->W) + 1;
+    if (c->discrete_ok && ((long long)cost_max + 4LL * c->p2_all) * n >= (1LL << 30))
+        return DM_ERR_RANGE;
+    set_path(c, cost_max, user_weights);
     if (!c->discrete_ok) return DM_OK;  // weights only feed the continuous stage
     DM_CK(dm::launch_validate_edges(c->ws + c->lay.wh, c->ws + c->lay.wv, c->H, c->W,
                                     reinterpret_cast<const int32_t*>(c->ws + c->lay.taps),
@@ -398,6 +373,19 @@ int census_cost(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right)
 }
 
 }  // namespace
+
+namespace dm {
+namespace ctxops {
+PdArgs pd_args(dm_ctx* c) { return ::pd_args(c); }
+Dmm16Args dm16_args(dm_ctx* c, int which) { return ::dm16_args(c, which); }
+int run_pass(dm_ctx* c, int which, uint16_t* labels, long long* lb)
+{
+    return ::run_pass(c, which, labels, lb);
+}
+void predict_path(dm_ctx* c, int cost_max) { ::set_path(c, cost_max, false); }
+size_t base_bytes(const dm_ctx* c) { return ::base_bytes(c); }
+}  // namespace ctxops
+}  // namespace dm
 
 namespace dm {
 // Penalty taps of one edge weight (shared with the allocation-free entry point).

@@ -74,6 +74,19 @@ struct Dmm16Args {
     int seg_cap;             // entries of each segment-start array: 2^ceil(log2 n) + 1, padded
 };
 
+// Persistent batched form of the 16-bit pass over the chains of up to
+// kBatchDescs pairs of one label class (dmm16_impl.cuh).  The descriptors travel
+// in the kernel's parameter space, like the single-pair kernel's arguments.
+constexpr int kBatchDescs = 96;
+struct Batch16Args {
+    const int2* tasks;       // (descriptor, chain), longest chains first
+    int n_tasks;
+    int* counter;            // work counter, zero at launch
+    int grid;                // CTAs
+    int n_desc;
+    Dmm16Args descs[kBatchDescs];  // labels, lb: set for this launch (nullable)
+};
+
 struct PdArgs {
     int H, W, L;
     const uint8_t* cost;     // [H][W][L] uint8 samples, used when the others are null
@@ -99,6 +112,18 @@ struct PdArgs {
     float* pv2;
     float* qh2;
     float* qv2;
+};
+
+// Batched primal-dual kernels (pd.cu): two descriptors per pair (set 0 -> set 1
+// and set 1 -> set 0), the first tile and the first pixel of each pair.
+struct PdBatchArgs {
+    const PdArgs* descs;        // [2 n]: descs[2 p + parity]
+    const int* tile_start;      // [n + 1] for the launch's tile shape
+    const long long* px_start;  // [n + 1]
+    const uint16_t* const* labels;  // [n] device pointers (init)
+    int n, total_tiles;
+    long long total_px;
+    int parity;
 };
 
 // Reverse of one primal-dual iteration k (pd.cu): state k (u, p, q) and
@@ -191,6 +216,8 @@ cudaError_t launch_cost(const uint32_t* census, int H, int W, int L, int maxc, v
 cudaError_t launch_dmm_pass(const DmmArgs& a, int lpt, int radius, cudaStream_t s);
 
 // dmm16.cu
+cudaError_t launch_dmm16_batch(const Batch16Args& b, int np, int radius, bool pad, int delta_bytes,
+                               cudaStream_t s);
 cudaError_t launch_dmm16_pass(const Dmm16Args& a, int np, int radius, int delta_bytes,
                               cudaStream_t s);
 cudaError_t launch_validate_edges(const uint8_t* wh, const uint8_t* wv, int H, int W,
@@ -209,6 +236,10 @@ cudaError_t launch_init_u_from_labels(const uint16_t* labels, float* u, int n, c
 cudaError_t launch_linearise(const PdArgs& a, cudaStream_t s);
 cudaError_t launch_pd_iter(const PdArgs& a, cudaStream_t s);
 cudaError_t launch_pd_adjoint(const AdjArgs& a, cudaStream_t s);
+bool pd_tile_supported(int tx, int ty);
+cudaError_t launch_pd_batch(const PdBatchArgs& b, int tx, int ty, int grid, cudaStream_t s);
+cudaError_t launch_lin_batch(const PdBatchArgs& b, int grid, cudaStream_t s);
+cudaError_t launch_init_batch(const PdBatchArgs& b, int grid, cudaStream_t s);
 cudaError_t launch_lin_adjoint(const LinAdjArgs& a, cudaStream_t s);
 cudaError_t launch_lin_jvp(const JvpArgs& a, cudaStream_t s);
 cudaError_t launch_pd_jvp(const JvpArgs& a, cudaStream_t s);

@@ -95,11 +95,8 @@ __global__ void zero_kernel(float* __restrict__ p, size_t n)
 // Linearisation of the data term around u0 = u (Sec. 3.1): slopes s1 (left of
 // u0) and s2 (right of u0), both set to their mean when s2 < s1, and the box
 // [u0 - h, u0 + h] intersected with [0, L-1].
-__global__ void linearise_kernel(const PdArgs A)
+__device__ __forceinline__ void lin_one(const PdArgs& A, int i)
 {
-    const int n = A.H * A.W;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
     const float u0 = A.u[i];
     const LinPx l = lin_px(cost_src(A), A.L, i, alpha_of(A.alpha_px, A.alpha, i), u0, A.h);
     float s1 = l.s1, s2 = l.s2;
@@ -112,6 +109,12 @@ __global__ void linearise_kernel(const PdArgs A)
     A.s2[i] = s2;
     A.lo[i] = fmaxf(__fsub_rn(u0, A.h), 0.0f);
     A.hi[i] = fminf(__fadd_rn(u0, A.h), (float)(A.L - 1));
+}
+
+__global__ void linearise_kernel(const PdArgs A)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < A.H * A.W) lin_one(A, i);
 }
 
 // prox of step * (omega r_{a,b})*: identity on |t| <= a omega, else shrink by
@@ -209,14 +212,17 @@ __device__ __forceinline__ float u_step(const PdArgs& A, int x, int y)
     return fminf(fmaxf(v, A.lo[i]), A.hi[i]);
 }
 
-__global__ void __launch_bounds__(kTX * kTY) pd_fused_kernel(const PdArgs A)
+// One TX x TY tile of the fused iteration: u+ on the tile and a one-pixel halo
+// to the right and below (from the old p, q), then the tile's edges.  The whole
+// CTA (TX * TY threads) calls it; there is no early exit, so a persistent loop
+// may call it again after a barrier.
+template <int TX, int TY>
+__device__ __forceinline__ void pd_tile(const PdArgs& A, int x0, int y0, float (*s_un)[TX + 1],
+                                        float (*s_u)[TX + 1])
 {
-    __shared__ float s_un[kTY + 1][kTX + 1];  // u+ on the tile and its right/lower halo
-    __shared__ float s_u[kTY + 1][kTX + 1];   // old u there
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int W = A.W, H = A.H;
-    for (int t = threadIdx.x; t < (kTX + 1) * (kTY + 1); t += kTX * kTY) {
-        const int lx = t % (kTX + 1), ly = t / (kTX + 1);
+    for (int t = threadIdx.x; t < (TX + 1) * (TY + 1); t += TX * TY) {
+        const int lx = t % (TX + 1), ly = t / (TX + 1);
         const int x = x0 + lx, y = y0 + ly;
         if (x < W && y < H) {
             s_un[ly][lx] = u_step(A, x, y);
@@ -224,26 +230,89 @@ __global__ void __launch_bounds__(kTX * kTY) pd_fused_kernel(const PdArgs A)
         }
     }
     __syncthreads();
-    const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
+    const int lx = threadIdx.x % TX, ly = threadIdx.x / TX;
     const int x = x0 + lx, y = y0 + ly;
-    if (x >= W || y >= H) return;
-    const int i = y * W + x;
-    const float ui = s_u[ly][lx];
-    const float uni = s_un[ly][lx];
-    A.u_new[i] = uni;
-    if (x + 1 < W) {
-        const float om = __fmul_rn(A.lambda_r, (float)A.wh[i]);
-        const float uj = s_u[ly][lx + 1];
-        A.qh2[i] = prox_conj(q_arg(A.qh[i], A.tau, ui, uj), om, 0.0f, A.bq, A.tau);
-        A.ph2[i] = prox_conj(p_arg(A.ph[i], A.sigma, ui, uni, uj, s_un[ly][lx + 1]), om, A.ap, A.bp,
-                             A.sigma);
+    if (x < W && y < H) {
+        const int i = y * W + x;
+        const float ui = s_u[ly][lx];
+        const float uni = s_un[ly][lx];
+        A.u_new[i] = uni;
+        if (x + 1 < W) {
+            const float om = __fmul_rn(A.lambda_r, (float)A.wh[i]);
+            const float uj = s_u[ly][lx + 1];
+            A.qh2[i] = prox_conj(q_arg(A.qh[i], A.tau, ui, uj), om, 0.0f, A.bq, A.tau);
+            A.ph2[i] = prox_conj(p_arg(A.ph[i], A.sigma, ui, uni, uj, s_un[ly][lx + 1]), om, A.ap,
+                                 A.bp, A.sigma);
+        }
+        if (y + 1 < H) {
+            const float om = __fmul_rn(A.lambda_r, (float)A.wv[i]);
+            const float uj = s_u[ly + 1][lx];
+            A.qv2[i] = prox_conj(q_arg(A.qv[i], A.tau, ui, uj), om, 0.0f, A.bq, A.tau);
+            A.pv2[i] = prox_conj(p_arg(A.pv[i], A.sigma, ui, uni, uj, s_un[ly + 1][lx]), om, A.ap,
+                                 A.bp, A.sigma);
+        }
     }
-    if (y + 1 < H) {
-        const float om = __fmul_rn(A.lambda_r, (float)A.wv[i]);
-        const float uj = s_u[ly + 1][lx];
-        A.qv2[i] = prox_conj(q_arg(A.qv[i], A.tau, ui, uj), om, 0.0f, A.bq, A.tau);
-        A.pv2[i] = prox_conj(p_arg(A.pv[i], A.sigma, ui, uni, uj, s_un[ly + 1][lx]), om, A.ap, A.bp,
-                             A.sigma);
+}
+
+__global__ void __launch_bounds__(kTX * kTY) pd_fused_kernel(const PdArgs A)
+{
+    __shared__ float s_un[kTY + 1][kTX + 1];  // u+ on the tile and its right/lower halo
+    __shared__ float s_u[kTY + 1][kTX + 1];   // old u there
+    pd_tile<kTX, kTY>(A, blockIdx.x * kTX, blockIdx.y * kTY, s_un, s_u);
+}
+
+// --- batched forms over many pairs (one launch per iteration for all pairs) ---
+
+// the pair whose range [start[p], start[p + 1]) holds t (start is ascending)
+template <typename T>
+__device__ __forceinline__ int pair_of(const T* start, int n, T t)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// persistent: the CTAs stride over the tiles of all pairs
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) pd_batch_kernel(const PdBatchArgs B)
+{
+    __shared__ float s_un[TY + 1][TX + 1];
+    __shared__ float s_u[TY + 1][TX + 1];
+    for (int t = blockIdx.x; t < B.total_tiles; t += gridDim.x) {
+        const int p = pair_of(B.tile_start, B.n, t);
+        const PdArgs& A = B.descs[2 * p + B.parity];
+        const int local = t - B.tile_start[p];
+        const int tx = (A.W + TX - 1) / TX;
+        pd_tile<TX, TY>(A, (local % tx) * TX, (local / tx) * TY, s_un, s_u);
+        __syncthreads();
+    }
+}
+
+// linearisation of every pixel of every pair (the current set of each pair)
+__global__ void lin_batch_kernel(const PdBatchArgs B)
+{
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < B.total_px;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int p = pair_of(B.px_start, B.n, g);
+        lin_one(B.descs[2 * p + B.parity], (int)(g - B.px_start[p]));
+    }
+}
+
+// u = labels in set 0, p = q = 0 in both sets, for every pair
+__global__ void init_batch_kernel(const PdBatchArgs B)
+{
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < B.total_px;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int p = pair_of(B.px_start, B.n, g);
+        const int i = (int)(g - B.px_start[p]);
+        const PdArgs& A = B.descs[2 * p];
+        A.u[i] = (float)B.labels[p][i];
+        A.ph[i] = A.pv[i] = A.qh[i] = A.qv[i] = 0.0f;
+        A.ph2[i] = A.pv2[i] = A.qh2[i] = A.qv2[i] = 0.0f;
     }
 }
 
@@ -653,6 +722,41 @@ cudaError_t launch_pd_iter(const PdArgs& a, cudaStream_t s)
 {
     dim3 grd((a.W + kTX - 1) / kTX, (a.H + kTY - 1) / kTY);
     pd_fused_kernel<<<grd, kTX * kTY, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TX, int TY>
+cudaError_t launch_pd_batch_t(const PdBatchArgs& b, int grid, cudaStream_t s)
+{
+    pd_batch_kernel<TX, TY><<<grid, TX * TY, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+bool pd_tile_supported(int tx, int ty)
+{
+    return (tx == 32 && (ty == 4 || ty == 8 || ty == 16)) || (tx == 64 && (ty == 4 || ty == 8)) ||
+           (tx == 16 && ty == 16);
+}
+
+cudaError_t launch_pd_batch(const PdBatchArgs& b, int tx, int ty, int grid, cudaStream_t s)
+{
+    if (tx == 32 && ty == 4) return launch_pd_batch_t<32, 4>(b, grid, s);
+    if (tx == 32 && ty == 16) return launch_pd_batch_t<32, 16>(b, grid, s);
+    if (tx == 64 && ty == 4) return launch_pd_batch_t<64, 4>(b, grid, s);
+    if (tx == 64 && ty == 8) return launch_pd_batch_t<64, 8>(b, grid, s);
+    if (tx == 16 && ty == 16) return launch_pd_batch_t<16, 16>(b, grid, s);
+    return launch_pd_batch_t<32, 8>(b, grid, s);
+}
+
+cudaError_t launch_lin_batch(const PdBatchArgs& b, int grid, cudaStream_t s)
+{
+    lin_batch_kernel<<<grid, 256, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_batch(const PdBatchArgs& b, int grid, cudaStream_t s)
+{
+    init_batch_kernel<<<grid, 256, 0, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -75,6 +75,20 @@ def lib() -> ctypes.CDLL:
             "dm_sync": [_vp],
             "dm_launch_count": [_vp, ctypes.POINTER(ctypes.c_uint64)],
             "dm_get_path": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+            "dm_batch_create": [_i, _vp, _vp, _vp, ctypes.POINTER(DmParams), ctypes.POINTER(_vp)],
+            "dm_batch_destroy": [_vp],
+            "dm_batch_workspace_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
+            "dm_batch_bind_workspace": [_vp, _vp, ctypes.c_size_t],
+            "dm_batch_set_stream": [_vp, _vp],
+            "dm_batch_context": [_vp, _i, ctypes.POINTER(_vp)],
+            "dm_batch_solve": [_vp, _vp, _vp, _i, _i, _vp],
+            "dm_batch_capture": [_vp, _vp, _vp, _i, _i, _vp],
+            "dm_batch_replay": [_vp],
+            "dm_batch_sync": [_vp],
+            "dm_batch_tune": [_vp, _vp, _vp, ctypes.c_char_p, _vp],
+            "dm_batch_set_tuning": [_vp, _vp],
+            "dm_batch_get_tuning": [_vp, _vp],
+            "dm_batch_launch_count": [_vp, ctypes.POINTER(ctypes.c_uint64)],
             "dm_discrete_pass_noalloc": [_i, _i, _i, ctypes.POINTER(DmParams), _i, _vp, _vp,
                                          _vp, _vp, _vp, _vp],
             "dm_set_cost_volume_f32": [_vp, _vp, _vp, _vp],
@@ -358,6 +372,142 @@ class Context:
 
     def sync(self):
         _ck(lib().dm_sync(self._h), "dm_sync")
+
+
+class _PairView(Context):
+    """The context of one pair of a Batch (owned by the batch)."""
+
+    def __init__(self, batch, i, H, W, L, params):
+        self._torch = batch._torch
+        self.H, self.W, self.L = H, W, L
+        self.params = params
+        self.device = batch.device
+        self.stream = batch.stream
+        self._tape = None
+        h = _vp()
+        _ck(lib().dm_batch_context(batch._h, i, ctypes.byref(h)), "dm_batch_context")
+        self._h = h
+        self._batch = batch
+
+    def close(self):
+        self._h = None
+
+    # the getters enqueue copies on the batch's stream: wait for them before torch
+    # (on its own stream) reads the results
+    def labels(self):
+        out = super().labels()
+        self.stream.synchronize()
+        return out
+
+    def disparity(self):
+        out = super().disparity()
+        self.stream.synchronize()
+        return out
+
+    def cost(self):
+        out = super().cost()
+        self.stream.synchronize()
+        return out
+
+
+class Batch:
+    """dm_batch: pairs of mixed sizes solved by persistent kernels, optionally
+    as one captured CUDA graph.  shapes: list of (H, W, L)."""
+
+    def __init__(self, shapes, params: DmParams | None = None, device: str = "cuda"):
+        import torch
+        self._torch = torch
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        self.n = len(self.shapes)
+        self.params = params if params is not None else default_params()
+        arr = lambda k: (ctypes.c_int * self.n)(*[s[k] for s in self.shapes])
+        h = _vp()
+        _ck(lib().dm_batch_create(self.n, arr(0), arr(1), arr(2), ctypes.byref(self.params),
+                                  ctypes.byref(h)), "dm_batch_create")
+        self._h = h
+        nb = ctypes.c_size_t()
+        _ck(lib().dm_batch_workspace_bytes(self._h, ctypes.byref(nb)), "dm_batch_workspace_bytes")
+        self.workspace_bytes = nb.value
+        self.device = torch.device(device)
+        self.stream = torch.cuda.Stream(self.device)   # capturable (not the legacy stream)
+        self._ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+        _ck(lib().dm_batch_set_stream(self._h, _vp(self.stream.cuda_stream)), "dm_batch_set_stream")
+        _ck(lib().dm_batch_bind_workspace(self._h, self._ws.data_ptr(), self.workspace_bytes),
+            "dm_batch_bind_workspace")
+        self.pairs = [_PairView(self, i, *self.shapes[i], self.params) for i in range(self.n)]
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ptrs(self, ts):
+        return (ctypes.c_void_p * self.n)(*[None if t is None else t.data_ptr() for t in ts])
+
+    def _inputs(self, lefts, rights):
+        torch = self._torch
+        dev = lambda a: (torch.as_tensor(np.ascontiguousarray(a)) if isinstance(a, np.ndarray)
+                         else a).to(self.device, torch.uint8).contiguous()
+        ls, rs = [dev(a) for a in lefts], [dev(a) for a in rights]
+        # the copies ran on torch's stream; the batch reads them on its own
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        return ls, rs
+
+    def outputs(self):
+        return [self._torch.empty((H, W), dtype=self._torch.float32, device=self.device)
+                for H, W, _ in self.shapes]
+
+    def solve(self, lefts, rights, dmm_iters: int, pd_iters: int, outs=None):
+        ls, rs = self._inputs(lefts, rights)
+        outs = outs if outs is not None else self.outputs()
+        self._keep = (ls, rs, outs)
+        _ck(lib().dm_batch_solve(self._h, self._ptrs(ls), self._ptrs(rs), dmm_iters, pd_iters,
+                                 self._ptrs(outs)), "dm_batch_solve")
+        return outs
+
+    def capture(self, lefts, rights, dmm_iters: int, pd_iters: int, outs):
+        """Record one solve on these device buffers (torch tensors that stay
+        alive and in place) into the batch's CUDA graph."""
+        self._graph_keep = (list(lefts), list(rights), list(outs))
+        self._torch.cuda.synchronize(self.device)
+        _ck(lib().dm_batch_capture(self._h, self._ptrs(lefts), self._ptrs(rights), dmm_iters,
+                                   pd_iters, self._ptrs(outs)), "dm_batch_capture")
+
+    def replay(self):
+        """Launch the captured graph after the work queued on torch's stream
+        (e.g. new inputs copied into the captured buffers)."""
+        self.stream.wait_stream(self._torch.cuda.current_stream(self.device))
+        _ck(lib().dm_batch_replay(self._h), "dm_batch_replay")
+
+    def sync(self):
+        _ck(lib().dm_batch_sync(self._h), "dm_batch_sync")
+
+    def tune(self, lefts, rights, cache_path: str | None = None):
+        ls, rs = self._inputs(lefts, rights)
+        out = (ctypes.c_int * 5)()
+        _ck(lib().dm_batch_tune(self._h, self._ptrs(ls), self._ptrs(rs),
+                                cache_path.encode() if cache_path else None, out), "dm_batch_tune")
+        return tuple(out)
+
+    def set_tuning(self, choice):
+        _ck(lib().dm_batch_set_tuning(self._h, (ctypes.c_int * 5)(*choice)), "dm_batch_set_tuning")
+
+    def tuning(self):
+        out = (ctypes.c_int * 5)()
+        _ck(lib().dm_batch_get_tuning(self._h, out), "dm_batch_get_tuning")
+        return tuple(out)
+
+    def launch_count(self) -> int:
+        n = ctypes.c_uint64()
+        _ck(lib().dm_batch_launch_count(self._h, ctypes.byref(n)), "dm_batch_launch_count")
+        return n.value
 
 
 def discrete_pass_noalloc(params: DmParams, which: int, cost, wedge, lam_in, lam_out,

@@ -140,3 +140,39 @@ def test_differentiable_calls_check_state_without_gpu(lib):
     assert lib.dm_set_lambda_r(h, 2.5) == dm.DM_OK
     assert lib.dm_set_lambda_r(None, 1.0) == dm.DM_ERR_ARG
     assert lib.dm_destroy(h) == 0
+
+
+def test_batch_create_and_workspace_without_gpu(lib):
+    from paper_1601_06274_gb300 import dm
+    p = dm.default_params()
+    n = 3
+    H = (ctypes.c_int * n)(240, 480, 375)
+    W = (ctypes.c_int * n)(320, 640, 1242)
+    L = (ctypes.c_int * n)(32, 64, 128)
+    b = ctypes.c_void_p()
+    assert lib.dm_batch_create(n, H, W, L, ctypes.byref(p), ctypes.byref(b)) == 0
+    nb = ctypes.c_size_t()
+    assert lib.dm_batch_workspace_bytes(b, ctypes.byref(nb)) == 0
+    single = 0
+    for i in range(n):
+        h = ctypes.c_void_p()
+        assert lib.dm_create(H[i], W[i], L[i], ctypes.byref(p), ctypes.byref(h)) == 0
+        s = ctypes.c_size_t()
+        lib.dm_workspace_bytes(h, ctypes.byref(s))
+        single += s.value
+        lib.dm_destroy(h)
+    assert nb.value >= single
+    ptrs = (ctypes.c_void_p * n)(1, 2, 3)
+    assert lib.dm_batch_solve(b, ptrs, ptrs, 5, 50, None) == dm.DM_ERR_STATE  # no workspace
+    assert lib.dm_batch_solve(b, ptrs, ptrs, 0, 50, None) == dm.DM_ERR_ARG
+    assert lib.dm_batch_solve(b, ptrs, ptrs, 257, 50, None) == dm.DM_ERR_ARG
+    assert lib.dm_batch_replay(b) == dm.DM_ERR_STATE                         # nothing captured
+    good = (ctypes.c_int * 5)(2, 32, 8, 4, 96)
+    bad = (ctypes.c_int * 5)(2, 48, 8, 4, 96)
+    assert lib.dm_batch_set_tuning(b, good) == 0 and lib.dm_batch_set_tuning(b, bad) == dm.DM_ERR_ARG
+    out = (ctypes.c_int * 5)()
+    assert lib.dm_batch_get_tuning(b, out) == 0 and tuple(out) == (2, 32, 8, 4, 96)
+    bad_H = (ctypes.c_int * n)(240, 0, 375)
+    b2 = ctypes.c_void_p()
+    assert lib.dm_batch_create(n, bad_H, W, L, ctypes.byref(p), ctypes.byref(b2)) == dm.DM_ERR_ARG
+    assert lib.dm_batch_destroy(b) == 0
