@@ -360,6 +360,11 @@ def roofline_line(ctx, avg, HW, L, cost_bytes, kernel_names):
 
 
 KERNEL_NAMES = {16: "dmm16_kernel", 32: "dmm_pass_kernel"}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from the ncu capture in
+# profiles/dmm16_kernel_kitti_1242x375x128.md (the 1242x375x128 frame, uint8
+# deltas); other workloads and kernels report null
+NCU_TRAFFIC = {("kitti", "dmm16_kernel horizontal pass"): 351_868_928,
+               ("kitti", "dmm16_kernel vertical pass"): 289_143_808}
 
 
 # ---------------------------------------------------------------------------
@@ -672,6 +677,7 @@ def main():
     # ---- dominant kernel: one Dual MM pass per launch, CUDA events on the ctx stream
     avg = time_passes(ctx, d_left, d_right, NI, max(1, args.steps // 2), flush, stream)
     roofline = roofline_line(ctx, avg, H * W, L, 1, KERNEL_NAMES)
+    roofline["traffic"] = NCU_TRAFFIC.get(("kitti", roofline["kernel"]))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
