@@ -479,26 +479,16 @@ __device__ __forceinline__ void sweep16(const Dmm16Args& A, const Ctx16& C, cons
         uint8_t* blk = ring + (bi & 1) * G::BLK;
         const int kb = k0 + dir * kBlk * bi;
         const int cnt = min(count - kBlk * bi, kBlk);
-        if (cnt == kBlk) {
-#pragma unroll 4
-            for (int u = 0; u < kBlk; ++u) {
-                const int k = kb + dir * u;
-                sweep_step<NP, R, PAD, DT>(C, s_taps, blk, u, k, dir, msg, off, lane, pad);
-                if (k + dir == next) {
-                    store_msg<NP>(sbuf, sofs, C, k + dir, lane, msg, off);
-                    --sp.t;
-                    next = sp.pos();
-                }
-            }
-        } else {
-            for (int u = 0; u < cnt; ++u) {
-                const int k = kb + dir * u;
-                sweep_step<NP, R, PAD, DT>(C, s_taps, blk, u, k, dir, msg, off, lane, pad);
-                if (k + dir == next) {
-                    store_msg<NP>(sbuf, sofs, C, k + dir, lane, msg, off);
-                    --sp.t;
-                    next = sp.pos();
-                }
+        // one copy of the step (each step depends on the previous message, so
+        // unrolling buys no overlap, only instruction-cache footprint)
+#pragma unroll 1
+        for (int u = 0; u < cnt; ++u) {
+            const int k = kb + dir * u;
+            sweep_step<NP, R, PAD, DT>(C, s_taps, blk, u, k, dir, msg, off, lane, pad);
+            if (k + dir == next) {
+                store_msg<NP>(sbuf, sofs, C, k + dir, lane, msg, off);
+                --sp.t;
+                next = sp.pos();
             }
         }
         __syncwarp();
@@ -685,34 +675,26 @@ __device__ __forceinline__ void chain16(const Dmm16Args& A, int chain, uint8_t* 
             Node<NP> v = read_node<NP, DT>(sl_i, C, -1, lane, pad);
             finalise<NP, DT>(A, C, 0, lane, pad, v.th, v.base, v.cv, zero, 0, zero, 0, lb_acc);
         }
-    } else if (n <= 4) {
-        if (warp == 0) {
-            for (int k = 0; k < n; ++k) issue_node<NP, DT>(A, C, k, k + 1 < n ? k : -1, slots[k], lane);
-            cp_commit();
-            cp_wait<0>();
-            __syncwarp();
-            leaf_block<NP, R, PAD, DT>(A, C, s_taps, slots, 0, n - 1, zero, 0, zero, 0, lane, pad,
-                                       lb_acc);
-        }
     } else {
         int levels = 0;
         while ((1 << levels) < n) ++levels;
-        // ---- level 0: both halves swept in parallel, then the root Handshake
-        {
+        // ---- level 0: both halves swept in parallel, then the root Handshake (a
+        // chain of 2-4 nodes is a single leaf block, done by the depth-first walk)
+        if (n >= 5) {
             const int a = 0, b = n - 1;
             const int i = ((n + 1) >> 1) - 1, j = i + 1;
             uint32_t m[NP];
             int off = 0;
 #pragma unroll
             for (int p = 0; p < NP; ++p) m[p] = 0u;
-            if (warp == 0) {
-                sweep16<NP, R, PAD, DT>(A, C, s_taps, ring, a, +1, i - a, m, off, spine_fwd(a, i),
-                                        A.fmsg, A.fofs, lane, pad);
-                store_msg<NP>(A.fmsg, A.fofs, C, i, lane, m, off);
-            } else if (warp == 1) {
-                sweep16<NP, R, PAD, DT>(A, C, s_taps, ring, b, -1, b - j, m, off, spine_bwd(j, b),
-                                        A.bmsg, A.bofs, lane, pad);
-                store_msg<NP>(A.bmsg, A.bofs, C, j, lane, m, off);
+            if (warp < 2) {  // warp 0 sweeps [0, i] forward, warp 1 [j, n-1] backward
+                const bool f = warp == 0;
+                uint32_t* sbuf = f ? A.fmsg : A.bmsg;
+                int* sofs = f ? A.fofs : A.bofs;
+                sweep16<NP, R, PAD, DT>(A, C, s_taps, ring, f ? a : b, f ? 1 : -1, f ? i - a : b - j,
+                                        m, off, f ? spine_fwd(a, i) : spine_bwd(j, b), sbuf, sofs,
+                                        lane, pad);
+                store_msg<NP>(sbuf, sofs, C, f ? i : j, lane, m, off);
             }
             __syncthreads();
             if (warp == 0) {
@@ -743,9 +725,10 @@ __device__ __forceinline__ void chain16(const Dmm16Args& A, int chain, uint8_t* 
         // ancestors left at its own positions.  Segments of 2-4 nodes are leaf
         // blocks (their whole subtree at once).
         int level = 1;
-        bool dfs = false;
+        bool dfs = n <= 4;
         uint32_t stk[32];  // a | b << 16 | right << 31 (chains of at most 8192 nodes)
         int sp = 0;
+        if (dfs && warp == 0) stk[sp++] = (uint32_t)(n - 1) << 16;  // the whole chain [0, n-1]
         while (true) {
             int a = 0, b = -1;
             bool right = false;
@@ -804,19 +787,24 @@ __device__ __forceinline__ void chain16(const Dmm16Args& A, int chain, uint8_t* 
                 int oF, oB, oij, oji;
                 cp_wait<0>();
                 __syncwarp();
-                if (right) {
-                    // right child: Lin changed, left messages recomputed from a
-                    read_msg<NP>(sl_m0, lane, Fi, oF);
-                    read_msg<NP>(sl_m1, lane, Bj, oB);
-                    sweep16<NP, R, PAD, DT>(A, C, s_taps, ring, a, +1, i - a, Fi, oF,
-                                            spine_fwd(a, i), A.fmsg, A.fofs, lane, pad);
-                } else {
-                    // left child: Rin changed, right messages recomputed from b
-                    read_msg<NP>(sl_m0, lane, Bj, oB);
-                    read_msg<NP>(sl_m1, lane, Fi, oF);
-                    sweep16<NP, R, PAD, DT>(A, C, s_taps, ring, b, -1, b - j, Bj, oB,
-                                            spine_bwd(j, b), A.bmsg, A.bofs, lane, pad);
+                // right child: Lin changed, the left messages are recomputed from a;
+                // left child: Rin changed, the right messages are recomputed from b
+                uint32_t m[NP];
+                int om;
+                read_msg<NP>(sl_m0, lane, m, om);
+                if (right) read_msg<NP>(sl_m1, lane, Bj, oB);
+                else read_msg<NP>(sl_m1, lane, Fi, oF);
+                sweep16<NP, R, PAD, DT>(A, C, s_taps, ring, right ? a : b, right ? 1 : -1,
+                                        right ? i - a : b - j, m, om,
+                                        right ? spine_fwd(a, i) : spine_bwd(j, b),
+                                        right ? A.fmsg : A.bmsg, right ? A.fofs : A.bofs, lane, pad);
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    Fi[p] = right ? m[p] : Fi[p];
+                    Bj[p] = right ? Bj[p] : m[p];
                 }
+                oF = right ? om : oF;
+                oB = right ? oB : om;
                 const Node<NP> ni = read_node<NP, DT>(sl_i, C, i, lane, pad);
                 const Node<NP> nj = read_node<NP, DT>(sl_j, C, -1, lane, pad);
                 hs_core<NP, R, PAD>(ni, nj, taps_of<R>(s_taps, ni.om), Fi, oF, Bj, oB, pij, oij,
