@@ -578,16 +578,21 @@ DM_API int dm_reset_duals(dm_ctx* ctx)
     int rc = ready(ctx);
     if (rc) return rc;
     const size_t HWL = (size_t)ctx->H * ctx->W * ctx->L;
-    DM_CK(cudaMemsetAsync(ctx->ws + ctx->lay.lam_v, 0, HWL * sizeof(int32_t), ctx->stream));
-    DM_CK(cudaMemsetAsync(ctx->ws + ctx->lay.lam_h, 0, HWL * sizeof(int32_t), ctx->stream));
-    if (ctx->use16 && ctx->have_cost) {
-        // the 16-bit path keeps c + lambda_v in place of lambda_v: c for a cold start
+    if (!(ctx->use16 && ctx->have_cost)) {
+        DM_CK(cudaMemsetAsync(ctx->ws + ctx->lay.lam_v, 0, HWL * sizeof(int32_t), ctx->stream));
+        DM_CK(cudaMemsetAsync(ctx->ws + ctx->lay.lam_h, 0, HWL * sizeof(int32_t), ctx->stream));
+    } else {
+        // lambda_h = 0 in the packed storage (a base and deltas); the 16-bit path
+        // keeps c + lambda_v in place of lambda_v: c for a cold start
+        DM_CK(cudaMemsetAsync(ctx->ws + ctx->lay.lam_h, 0,
+                              base_bytes(ctx) + HWL * ctx->delta_bytes, ctx->stream));
         uint8_t* reg = ctx->ws + ctx->lay.lam_v;
         DM_CK(dm::launch_theta_h_init(ctx->ws + ctx->lay.cost, ctx->cost_bytes,
                                       reinterpret_cast<int32_t*>(reg),
                                       reg + base_bytes(ctx), ctx->delta_bytes,
                                       (long long)ctx->H * ctx->W, ctx->L, ctx->stream));
-        ctx->launches += 1;
+        // uint8 costs into uint8 deltas are a copy, not a kernel
+        if (!(ctx->cost_bytes == 1 && ctx->delta_bytes == 1)) ctx->launches += 1;
     }
     ctx->have_labels = false;
     return DM_OK;

@@ -146,6 +146,12 @@ cudaError_t launch_theta_h_init(const void* cost, int cost_bytes, int32_t* base,
                                 int delta_bytes, long long n_px, int L, cudaStream_t s)
 {
     const long long total = n_px * L;
+    if (cost_bytes == 1 && delta_bytes == 1) {
+        // the deltas are the cost bytes themselves, over a zero base
+        cudaError_t e = cudaMemsetAsync(base, 0, (size_t)n_px * sizeof(int32_t), s);
+        if (e != cudaSuccess) return e;
+        return cudaMemcpyAsync(delta, cost, (size_t)total, cudaMemcpyDeviceToDevice, s);
+    }
     theta_h_init_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
         cost, cost_bytes, base, delta, delta_bytes, n_px, L);
     return cudaGetLastError();
