@@ -363,7 +363,8 @@ KERNEL_NAMES = {16: "dmm16_kernel", 32: "dmm_pass_kernel"}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from the ncu capture in
 # profiles/ of the kernel as built now (keyed by workload and kernel); a kernel
 # changed since its capture has no entry and reports null
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("kitti", "dmm16_kernel horizontal pass"): 351_392_000,
+               ("kitti", "dmm16_kernel vertical pass"): 289_200_384}
 
 
 # ---------------------------------------------------------------------------
