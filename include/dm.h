@@ -29,8 +29,11 @@
  *     been synchronised.  Calls that return host data synchronise the stream.
  *   - Every entry point returns a status code (DM_OK on success).  No
  *     exception crosses the ABI.  Device-side faults detected by the kernels
- *     (e.g. an edge weight with no integer penalty table) are recorded in the
- *     workspace and reported as DM_ERR_DEVICE by the next synchronising call.
+ *     are recorded in the workspace and reported by the next synchronising
+ *     call: DM_ERR_RANGE for a dual outside the packed storage's range,
+ *     DM_ERR_DEVICE otherwise (e.g. an edge weight with no integer penalty
+ *     table).  No kernel waits on another, so DM_ERR_TIMEOUT is not returned.
+ *   - The main stages open NVTX ranges named after their entry points.
  *   - A context is not thread-safe: use one context per host thread.
  */
 #ifndef DM_H

@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dm_internal.cuh"
 
 #include "dm_ctx.cuh"
@@ -233,13 +235,21 @@ int make_plan(const dm_ctx* c, int iters, int ckpt, TapePlan* tp)
     return DM_OK;
 }
 
+// an NVTX range over one C ABI stage (a no-op unless a profiler listens)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
 int check_device_error(dm_ctx* c)
 {
     int32_t err = 0;
     DM_CK(cudaMemcpyAsync(&err, c->ws + c->lay.err, sizeof(err), cudaMemcpyDeviceToHost,
                           c->stream));
     DM_CK(cudaStreamSynchronize(c->stream));
-    return err != 0 ? DM_ERR_DEVICE : DM_OK;
+    if (err == 0) return DM_OK;
+    // a dual outside the packed storage's range has its own code
+    return (err & dm::kDevErrRange) != 0 ? DM_ERR_RANGE : DM_ERR_DEVICE;
 }
 
 int ready(const dm_ctx* c)
@@ -600,6 +610,7 @@ DM_API int dm_reset_duals(dm_ctx* ctx)
 
 DM_API int dm_cost_volume(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right)
 {
+    const Range range("dm_cost_volume");
     int rc = ready(ctx);
     if (rc) return rc;
     if (d_left == nullptr || d_right == nullptr) return DM_ERR_ARG;
@@ -609,6 +620,7 @@ DM_API int dm_cost_volume(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_r
 
 DM_API int dm_cost_volume_warm(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right)
 {
+    const Range range("dm_cost_volume_warm");
     int rc = ready(ctx);
     if (rc) return rc;
     if (d_left == nullptr || d_right == nullptr) return DM_ERR_ARG;
@@ -680,6 +692,7 @@ DM_API int dm_discrete_pass(dm_ctx* ctx, int which)
 
 DM_API int dm_discrete(dm_ctx* ctx, int iters, int64_t* h_lb)
 {
+    const Range range("dm_discrete");
     if (ctx == nullptr || iters < 1 || iters > kMaxIters || !ctx->discrete_ok) return DM_ERR_ARG;
     int rc = ready(ctx);
     if (rc) return rc;
@@ -703,6 +716,7 @@ DM_API int dm_discrete(dm_ctx* ctx, int iters, int64_t* h_lb)
 
 DM_API int dm_refine(dm_ctx* ctx, int iters, const float* d_u0)
 {
+    const Range range("dm_refine");
     int rc = ready(ctx);
     if (rc) return rc;
     if (iters < 0) return DM_ERR_ARG;
@@ -792,6 +806,7 @@ DM_API int dm_tape_bytes(const dm_ctx* ctx, int iters, int ckpt_every, size_t* b
 DM_API int dm_refine_tape(dm_ctx* ctx, int iters, int ckpt_every, const float* d_u0, void* d_tape,
                           size_t tape_bytes)
 {
+    const Range range("dm_refine_tape");
     int rc = ready(ctx);
     if (rc) return rc;
     TapePlan tp;
@@ -860,6 +875,7 @@ DM_API int dm_refine_tape(dm_ctx* ctx, int iters, int ckpt_every, const float* d
 DM_API int dm_refine_backward(dm_ctx* ctx, const float* d_gu, void* d_tape, size_t tape_bytes,
                               float* d_gcost, float* d_galpha, double* d_glambda, float* d_gu0)
 {
+    const Range range("dm_refine_backward");
     int rc = ready(ctx);
     if (rc) return rc;
     if (d_gu == nullptr) return DM_ERR_ARG;

@@ -25,6 +25,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dm_ctx.cuh"
 
 namespace {
@@ -316,6 +318,10 @@ int batch_pd(dm_batch* b, const Group& g, int iters)
 int batch_solve(dm_batch* b, const uint8_t* const* d_left, const uint8_t* const* d_right,
                 int dmm_iters, int pd_iters, float* const* d_u)
 {
+    nvtxRangePushA("dm_batch_solve");
+    struct Pop {
+        ~Pop() { nvtxRangePop(); }
+    } pop;
     int rc;
     const unsigned long long l0 = b->launches;
     for (int i = 0; i < b->n; ++i) {

@@ -32,6 +32,8 @@
 
 #pragma once
 
+#include <atomic>
+
 #include "dm_internal.cuh"
 
 namespace dm {
@@ -865,17 +867,31 @@ constexpr int smem16_fixed()
     return 256 * kTapW * 4 + kWarps * Geo<NP, DT>::WARP;
 }
 
+// Raise a kernel's dynamic shared-memory limit to smem on the current device.
+// The attribute belongs to the function on each device; `done` records, per
+// device, the size already set (safe to call from several host threads).
+constexpr int kMaxDevices = 64;
+
+template <typename K>
+cudaError_t ensure_smem(K kernel, int smem, std::atomic<int> (&done)[kMaxDevices])
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::atomic<int>& d = done[dev < kMaxDevices ? dev : kMaxDevices - 1];
+    if (d.load(std::memory_order_acquire) >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) d.store(smem, std::memory_order_release);
+    return e;
+}
+
 template <int NP, int R, bool PAD, typename DT>
 cudaError_t launch_one(const Dmm16Args& a, cudaStream_t s)
 {
     const int smem = smem16_fixed<NP, DT>();
-    static int configured = 0;  // largest size set so far (the attribute is per function)
-    if (smem > configured) {
-        const cudaError_t e = cudaFuncSetAttribute(dmm16_kernel<NP, R, PAD, DT>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    static std::atomic<int> done[kMaxDevices];
+    const cudaError_t e = ensure_smem(dmm16_kernel<NP, R, PAD, DT>, smem, done);
+    if (e != cudaSuccess) return e;
     const int chains = a.which == 0 ? a.H : a.W;
     dmm16_kernel<NP, R, PAD, DT><<<chains, kWarps * 32, smem, s>>>(a);
     return cudaGetLastError();
@@ -885,13 +901,9 @@ template <int NP, int R, bool PAD, typename DT>
 cudaError_t launch_batch_one(const Batch16Args& b, cudaStream_t s)
 {
     const int smem = smem16_fixed<NP, DT>();
-    static int configured = 0;
-    if (smem > configured) {
-        const cudaError_t e = cudaFuncSetAttribute(dmm16_batch_kernel<NP, R, PAD, DT>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    static std::atomic<int> done[kMaxDevices];
+    const cudaError_t e = ensure_smem(dmm16_batch_kernel<NP, R, PAD, DT>, smem, done);
+    if (e != cudaSuccess) return e;
     dmm16_batch_kernel<NP, R, PAD, DT><<<b.grid, kWarps * 32, smem, s>>>(b);
     return cudaGetLastError();
 }

@@ -581,6 +581,37 @@ def refine_differentiable(dmctx: Context, cost, alpha, lambda_r, u0, iters: int,
     return _refine_function().apply(cost, alpha, lambda_r, u0, dmctx, iters, ckpt_every)
 
 
+def solve(left, right, L: int, dmm_iters: int = 10, pd_iters: int = 100,
+          params: DmParams | None = None, device: str = "cuda"):
+    """One pair through the whole path: (refined u [H][W] float32 tensor, labels
+    [H][W] uint16 numpy, lower bound of every Dual MM iteration numpy int64)."""
+    H, W = np.asarray(left).shape if isinstance(left, np.ndarray) else tuple(left.shape)
+    ctx = Context(H, W, L, params, device=device)
+    u = ctx.solve(left, right, dmm_iters, pd_iters)
+    return u, labels_u16(ctx.labels()), ctx.lower_bounds(dmm_iters)
+
+
+def batch_solve(pairs, labels, dmm_iters: int = 5, pd_iters: int = 50,
+                params: DmParams | None = None, device: str = "cuda", tune: bool = True):
+    """Many pairs [(left, right), ...] with label counts `labels` (one per pair)
+    through the batched kernels: a list of (u, labels, lower bounds) as in solve."""
+    shapes = [(np.asarray(l).shape[0], np.asarray(l).shape[1], int(n))
+              for (l, _), n in zip(pairs, labels)]
+    b = Batch(shapes, params, device=device)
+    lefts, rights = [p[0] for p in pairs], [p[1] for p in pairs]
+    if tune:
+        b.tune(lefts, rights)
+    outs = b.solve(lefts, rights, dmm_iters, pd_iters)
+    b.sync()
+    return [(outs[i], labels_u16(b.pairs[i].labels()), b.pairs[i].lower_bounds(dmm_iters))
+            for i in range(b.n)]
+
+
+def DMRefine():
+    """The torch.autograd.Function behind refine_differentiable (built on first use)."""
+    return _refine_function()
+
+
 def labels_u16(t) -> np.ndarray:
     """int16 tensor holding uint16 labels -> numpy uint16."""
     return t.cpu().numpy().view(np.uint16)

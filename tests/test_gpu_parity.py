@@ -143,6 +143,43 @@ def test_discrete_labels_and_bounds(dm, H, W, L, iters, path):
     assert np.array_equal(lb, rlb)
     assert np.array_equal(labels, rl)
     assert np.all(np.diff(lb) >= 0)
+    assert lb[-1] <= O.discrete_energy(cost, wh, wv, labels)   # weak duality
+
+
+@pytest.mark.parametrize("H,W,L", [(7, 9, 16), (5, 33, 64), (9, 6, 128)])
+@pytest.mark.parametrize("path", [0, 1])
+def test_all_equal_costs_break_ties_to_the_smallest_label(dm, H, W, L, path):
+    cost = np.full((H, W, L), 7, dtype=np.uint8)
+    wh = np.full((H, W), 8, dtype=np.uint8)
+    wv = np.full((H, W), 4, dtype=np.uint8)
+    wh[:, -1] = 0
+    wv[-1, :] = 0
+    ctx = _ctx(dm, H, W, L, dmm_path=path)
+    ctx.set_cost_volume(cost, wh, wv)
+    _check_passes(dm, ctx, cost.astype(np.int32), wh.astype(np.int32), wv.astype(np.int32), 2,
+                  O.Params())
+    ctx.reset_duals()
+    lb = ctx.discrete(3, lower_bounds=True)
+    labels = dm.labels_u16(ctx.labels())
+    rl, rlb, _, _ = O.dmm(cost, wh, wv, 3)
+    assert np.array_equal(labels, rl) and np.array_equal(lb, rlb)
+    assert np.all(labels == 0)
+
+
+def test_module_level_solve_and_batch_solve(dm):
+    spec = S.SMALL
+    sp = S.make_workload(spec, seed=6)
+    u, labels, lb = dm.solve(sp.left, sp.right, spec["L"], spec["dmm_iters"], spec["pd_iters"])
+    ref = O.solve(sp.left, sp.right, spec["L"], spec["dmm_iters"], spec["pd_iters"])
+    assert np.array_equal(labels, ref["labels"]) and np.array_equal(lb, ref["lb"])
+    assert np.abs(u.cpu().numpy().astype(np.float64) - ref["u"]).max() <= U_TOL
+    pairs = [(sp.left, sp.right), (S.random_image(20, 30, 1), S.random_image(20, 30, 2))]
+    out = dm.batch_solve(pairs, [16, 32], spec["dmm_iters"], spec["pd_iters"], tune=False)
+    for (l, r), n, (bu, bl, blb) in zip(pairs, [16, 32], out):
+        rr = O.solve(l, r, n, spec["dmm_iters"], spec["pd_iters"])
+        assert np.array_equal(bl, rr["labels"]) and np.array_equal(blb, rr["lb"])
+        assert np.abs(bu.cpu().numpy().astype(np.float64) - rr["u"]).max() <= U_TOL
+    assert issubclass(dm.DMRefine(), __import__("torch").autograd.Function)
 
 
 def test_invalid_edge_weight_is_reported(dm):
