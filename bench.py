@@ -53,6 +53,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, ws: int, device) -> float:
+    """The slowest rank's time (an all-reduce MAX; the local value when alone)."""
+    if ws <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_step: int, steps: int, ws: int, tot_ms: float) -> float:
+    """Whole-job throughput in millions of units per second: every rank solves its
+    own frames (replicas, weak scaling), timed by the slowest rank."""
+    return units_per_step * steps * ws / (tot_ms / 1e3) / 1e6
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded crop (the cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
@@ -649,13 +665,9 @@ def main():
     launches = ctx.launch_count() - launches0
     ctx.sync()
     ms = [a.elapsed_time(b) for a, b in evs]
-    tot_ms = sum(ms)
-    t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(ms), ws, dev)
     units = H * W * L
-    value = units * args.steps * ws / (tot_ms / 1e3) / 1e6
+    value = job_value(units, args.steps, ws, tot_ms)
 
     # ---- end to end through the C ABI with pinned host buffers
     h_left = torch.from_numpy(sp.left).pin_memory()
