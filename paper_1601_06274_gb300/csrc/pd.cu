@@ -16,12 +16,24 @@
 // The cost samples are uint8 (census) or float32 (a caller's cost volume), the
 // data weight a scalar or a per-pixel map.
 
+#include <utility>
+
 #include "dm_internal.cuh"
 
 namespace dm {
 namespace {
 
 constexpr int kTX = 32, kTY = 8;
+
+// Programmatic dependent launch: an iteration kernel may be launched while the
+// previous one drains; it waits for that grid (and its memory) before reading,
+// and lets the next one launch once its own stores are issued.  Both are
+// no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_next_grid()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // the cost samples: float32, uint16 or uint8 (the first that is set)
 struct CostSrc {
@@ -113,8 +125,10 @@ __device__ __forceinline__ void lin_one(const PdArgs& A, int i)
 
 __global__ void linearise_kernel(const PdArgs A)
 {
+    wait_prior_grid();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < A.H * A.W) lin_one(A, i);
+    allow_next_grid();
 }
 
 // prox of step * (omega r_{a,b})*: identity on |t| <= a omega, else shrink by
@@ -258,7 +272,9 @@ __global__ void __launch_bounds__(kTX * kTY) pd_fused_kernel(const PdArgs A)
 {
     __shared__ float s_un[kTY + 1][kTX + 1];  // u+ on the tile and its right/lower halo
     __shared__ float s_u[kTY + 1][kTX + 1];   // old u there
+    wait_prior_grid();
     pd_tile<kTX, kTY>(A, blockIdx.x * kTX, blockIdx.y * kTY, s_un, s_u);
+    allow_next_grid();
 }
 
 // --- batched forms over many pairs (one launch per iteration for all pairs) ---
@@ -280,6 +296,7 @@ __device__ __forceinline__ int pair_of(const T* start, int n, T t)
 template <int TX, int TY>
 __global__ void __launch_bounds__(TX * TY) pd_batch_kernel(const PdBatchArgs B)
 {
+    wait_prior_grid();
     __shared__ float s_un[TY + 1][TX + 1];
     __shared__ float s_u[TY + 1][TX + 1];
     for (int t = blockIdx.x; t < B.total_tiles; t += gridDim.x) {
@@ -290,16 +307,19 @@ __global__ void __launch_bounds__(TX * TY) pd_batch_kernel(const PdBatchArgs B)
         pd_tile<TX, TY>(A, (local % tx) * TX, (local / tx) * TY, s_un, s_u);
         __syncthreads();
     }
+    allow_next_grid();
 }
 
 // linearisation of every pixel of every pair (the current set of each pair)
 __global__ void lin_batch_kernel(const PdBatchArgs B)
 {
+    wait_prior_grid();
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < B.total_px;
          g += (long long)gridDim.x * blockDim.x) {
         const int p = pair_of(B.px_start, B.n, g);
         lin_one(B.descs[2 * p + B.parity], (int)(g - B.px_start[p]));
     }
+    allow_next_grid();
 }
 
 // u = labels in set 0, p = q = 0 in both sets, for every pair
@@ -373,6 +393,7 @@ constexpr int kPX = kTX + 1, kPY = kTY + 1;  // pixels x0 .. x0+kTX, y0 .. y0+kT
 
 __global__ void __launch_bounds__(kTX * kTY) pd_adjoint_kernel(const AdjArgs A)
 {
+    wait_prior_grid();
     __shared__ float s_tph[kEY][kEX], s_tpv[kEY][kEX], s_tqh[kEY][kEX], s_tqv[kEY][kEX];
     __shared__ float s_uhb[kPY][kPX];
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
@@ -480,6 +501,7 @@ __global__ void __launch_bounds__(kTX * kTY) pd_adjoint_kernel(const AdjArgs A)
     A.qhb2[i] = qhb;
     A.pvb2[i] = pvb;
     A.qvb2[i] = qvb;
+    allow_next_grid();
 }
 
 // d D_i(x) / dx of the clamped interpolation (zero outside [0, L-1])
@@ -508,6 +530,7 @@ __device__ __forceinline__ void interp_dc(float* g, int L, float x, float w)
 // the accumulators are cleared for the previous warp.
 __global__ void lin_adjoint_kernel(const LinAdjArgs A)
 {
+    wait_prior_grid();
     const int n = A.H * A.W;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -532,6 +555,7 @@ __global__ void lin_adjoint_kernel(const LinAdjArgs A)
     A.gu0[i] = 0.0f;
     A.gs1[i] = 0.0f;
     A.gs2[i] = 0.0f;
+    allow_next_grid();
 }
 
 // ---------------------------------------------------------------------------
@@ -543,6 +567,7 @@ __global__ void lin_adjoint_kernel(const LinAdjArgs A)
 // linearisation of a warp and its tangent (u0 = u at the warp start)
 __global__ void lin_jvp_kernel(const JvpArgs J)
 {
+    wait_prior_grid();
     const PdArgs& A = J.f;
     const int n = A.H * A.W;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -580,10 +605,12 @@ __global__ void lin_jvp_kernel(const JvpArgs J)
     J.ds2[i] = ds2;
     J.dlo[i] = um > 0.0f ? du0 : 0.0f;
     J.dhi[i] = up < (float)(A.L - 1) ? du0 : 0.0f;
+    allow_next_grid();
 }
 
 __global__ void __launch_bounds__(kTX * kTY) pd_jvp_kernel(const JvpArgs J)
 {
+    wait_prior_grid();
     const PdArgs& A = J.f;
     __shared__ float s_un[kTY + 1][kTX + 1], s_u[kTY + 1][kTX + 1];
     __shared__ float s_dun[kTY + 1][kTX + 1], s_du[kTY + 1][kTX + 1];
@@ -661,6 +688,7 @@ __global__ void __launch_bounds__(kTX * kTY) pd_jvp_kernel(const JvpArgs J)
         J.dqv2[i] = 0.0f;
         J.dpv2[i] = 0.0f;
     }
+    allow_next_grid();
 }
 
 constexpr int kSumThreads = 256, kSumBlocks = 152;
@@ -711,25 +739,39 @@ cudaError_t launch_zero_f32(float* p, size_t n, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// launch with programmatic stream serialisation (see wait_prior_grid)
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, cudaStream_t s, A&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
 cudaError_t launch_linearise(const PdArgs& a, cudaStream_t s)
 {
     const int n = a.H * a.W;
-    linearise_kernel<<<(n + 255) / 256, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(linearise_kernel, dim3((n + 255) / 256), dim3(256), s, a);
 }
 
 cudaError_t launch_pd_iter(const PdArgs& a, cudaStream_t s)
 {
     dim3 grd((a.W + kTX - 1) / kTX, (a.H + kTY - 1) / kTY);
-    pd_fused_kernel<<<grd, kTX * kTY, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(pd_fused_kernel, grd, dim3(kTX * kTY), s, a);
 }
 
 template <int TX, int TY>
 cudaError_t launch_pd_batch_t(const PdBatchArgs& b, int grid, cudaStream_t s)
 {
-    pd_batch_kernel<TX, TY><<<grid, TX * TY, 0, s>>>(b);
-    return cudaGetLastError();
+    return launch_pdl(pd_batch_kernel<TX, TY>, dim3(grid), dim3(TX * TY), s, b);
 }
 
 bool pd_tile_supported(int tx, int ty)
@@ -750,8 +792,7 @@ cudaError_t launch_pd_batch(const PdBatchArgs& b, int tx, int ty, int grid, cuda
 
 cudaError_t launch_lin_batch(const PdBatchArgs& b, int grid, cudaStream_t s)
 {
-    lin_batch_kernel<<<grid, 256, 0, s>>>(b);
-    return cudaGetLastError();
+    return launch_pdl(lin_batch_kernel, dim3(grid), dim3(256), s, b);
 }
 
 cudaError_t launch_init_batch(const PdBatchArgs& b, int grid, cudaStream_t s)
@@ -763,29 +804,25 @@ cudaError_t launch_init_batch(const PdBatchArgs& b, int grid, cudaStream_t s)
 cudaError_t launch_pd_adjoint(const AdjArgs& a, cudaStream_t s)
 {
     dim3 grd((a.W + kTX - 1) / kTX, (a.H + kTY - 1) / kTY);
-    pd_adjoint_kernel<<<grd, kTX * kTY, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(pd_adjoint_kernel, grd, dim3(kTX * kTY), s, a);
 }
 
 cudaError_t launch_lin_adjoint(const LinAdjArgs& a, cudaStream_t s)
 {
     const int n = a.H * a.W;
-    lin_adjoint_kernel<<<(n + 255) / 256, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(lin_adjoint_kernel, dim3((n + 255) / 256), dim3(256), s, a);
 }
 
 cudaError_t launch_lin_jvp(const JvpArgs& a, cudaStream_t s)
 {
     const int n = a.f.H * a.f.W;
-    lin_jvp_kernel<<<(n + 255) / 256, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(lin_jvp_kernel, dim3((n + 255) / 256), dim3(256), s, a);
 }
 
 cudaError_t launch_pd_jvp(const JvpArgs& a, cudaStream_t s)
 {
     dim3 grd((a.f.W + kTX - 1) / kTX, (a.f.H + kTY - 1) / kTY);
-    pd_jvp_kernel<<<grd, kTX * kTY, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(pd_jvp_kernel, grd, dim3(kTX * kTY), s, a);
 }
 
 // partial must hold kSumBlocks doubles
