@@ -829,13 +829,18 @@ __device__ __forceinline__ void chain16(const Dmm16Args& A, int chain, uint8_t* 
 }
 
 
+// Launched with programmatic stream serialisation: the taps table (which no
+// pass writes) is staged while the previous pass drains; everything else waits
+// for that grid (griddepcontrol.wait).  Without the attribute both are no-ops.
 template <int NP, int R, bool PAD, typename DT>
 __global__ void __launch_bounds__(kWarps * 32, 3) dmm16_kernel(const Dmm16Args A)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t* s_taps = reinterpret_cast<uint32_t*>(smem);
     for (int t = threadIdx.x; t < 256 * kTapW; t += blockDim.x) s_taps[t] = A.taps16[t];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     chain16<NP, R, PAD, DT>(A, blockIdx.x, smem, s_taps);
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Persistent form over the chains of many pairs of one label class: every CTA
@@ -893,8 +898,17 @@ cudaError_t launch_one(const Dmm16Args& a, cudaStream_t s)
     const cudaError_t e = ensure_smem(dmm16_kernel<NP, R, PAD, DT>, smem, done);
     if (e != cudaSuccess) return e;
     const int chains = a.which == 0 ? a.H : a.W;
-    dmm16_kernel<NP, R, PAD, DT><<<chains, kWarps * 32, smem, s>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(chains);
+    cfg.blockDim = dim3(kWarps * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, dmm16_kernel<NP, R, PAD, DT>, a);
 }
 
 template <int NP, int R, bool PAD, typename DT>
