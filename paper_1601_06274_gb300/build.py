@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(CSRC, "_build")
 LIB = os.path.join(HERE, "libdm.so")
+LIB_CHECKED = os.path.join(HERE, "libdm_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
               "--expt-relaxed-constexpr"]
@@ -35,17 +36,23 @@ def _headers() -> list[str]:
     return hs
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False,
+          checked: bool = False) -> str:
+    """Compile libdm.so; with checked=True, libdm_checked.so: the same sources
+    with -DDM_CHECKED (index checks that report through the device error word),
+    for the memory-safety tests."""
+    obj_dir = OBJ + ("_checked" if checked else "")
+    lib = LIB_CHECKED if checked else LIB
+    os.makedirs(obj_dir, exist_ok=True)
     srcs = sources()
     newest_dep = max(os.path.getmtime(p) for p in srcs + _headers())
-    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest_dep):
-        return LIB
+    if (not force and os.path.exists(lib) and os.path.getmtime(lib) >= newest_dep):
+        return lib
     nvcc = _nvcc()
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *(["-DDM_CHECKED"] if checked else []), "-c", src, "-o", obj]
         if ptxas_v:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -57,13 +64,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
 
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -25,6 +25,7 @@ constexpr int kInf = 1 << 29;
 // device-side error codes written to the workspace error word
 constexpr int kDevErrBadOmega = 1;
 constexpr int kDevErrRange = 2;
+constexpr int kDevErrIndex = 4;  // checked builds: an index outside its array (access skipped)
 
 struct Layout {
     size_t cost, census, img, wh, wv, lam_h, lam_v, fmsg, bmsg, labels, lb, taps, taps16;

@@ -129,8 +129,24 @@ __device__ __forceinline__ void msg16(uint32_t (&a)[NP], uint32_t (&out)[NP], in
 struct Ctx16 {
     int which, H, W, L, n, c, KP2;  // KP2: packed registers per stored message (32 * NP)
     bool c16;                       // uint16 cost volume
+    int32_t* err;                   // the device error word
     __device__ __forceinline__ int pix(int k) const { return which == 0 ? c * W + k : k * W + c; }
 };
+
+// Checked builds (-DDM_CHECKED, the library's memory-safety test) verify every
+// node, edge and message position before a global access: a position outside
+// the chain sets kDevErrIndex and skips the access.  Otherwise the checks
+// compile away.
+#ifdef DM_CHECKED
+__device__ __forceinline__ bool in_chain(const Ctx16& C, int k, int limit)
+{
+    const bool ok = k >= 0 && k < limit && C.c >= 0 && C.c < (C.which == 0 ? C.H : C.W);
+    if (!ok) atomicOr(C.err, kDevErrIndex);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool in_chain(const Ctx16&, int, int) { return true; }
+#endif
 
 // ---------------------------------------------------------------------------
 // Asynchronous staging.  Unary rows and messages reach shared memory through
@@ -190,16 +206,19 @@ __device__ __forceinline__ void issue_block(const Dmm16Args& A, const Ctx16& C, 
     const int rowd = C.L * (int)sizeof(DT);
     const int part = rowd >> 2;
     const int u = lane >> 2, q = lane & 3;
-    if (u < cnt) {
+    if (u < cnt && in_chain(C, k0 + dir * u, C.n)) {
         const int pix = C.pix(k0 + dir * u);
         cp_bytes(blk + u * G::ROW + q * part,
                  reinterpret_cast<const uint8_t*>(A.delta_in) + (size_t)pix * rowd + q * part, part);
     }
-    if (lane < cnt) cp_async<4>(blk + kBlk * G::ROW + 4 * lane, A.base_in + C.pix(k0 + dir * lane));
+    if (lane < cnt && in_chain(C, k0 + dir * lane, C.n))
+        cp_async<4>(blk + kBlk * G::ROW + 4 * lane, A.base_in + C.pix(k0 + dir * lane));
     const int v = lane - 8;
     if (v >= 0 && v < cnt) {
         const int k = k0 + dir * v;
-        cp_async<4>(blk + kBlk * G::ROW + 32 + 4 * v, A.wedge + (C.pix(dir > 0 ? k : k - 1) & ~3));
+        const int e = dir > 0 ? k : k - 1;  // the edge (e, e + 1) the step crosses
+        if (in_chain(C, e, C.n - 1))
+            cp_async<4>(blk + kBlk * G::ROW + 32 + 4 * v, A.wedge + (C.pix(e) & ~3));
     }
 }
 
@@ -209,6 +228,7 @@ __device__ __forceinline__ void issue_node(const Dmm16Args& A, const Ctx16& C, i
                                            uint8_t* slot, int lane)
 {
     using G = Geo<NP, DT>;
+    if (!in_chain(C, k, C.n) || (edge >= 0 && !in_chain(C, edge, C.n - 1))) return;
     const int pix = C.pix(k);
     const int rowd = C.L * (int)sizeof(DT);
     const int part = rowd >> 2;
@@ -236,6 +256,7 @@ template <int NP>
 __device__ __forceinline__ void issue_msg(const uint32_t* buf, const int* ofs, const Ctx16& C,
                                           int pos, uint8_t* slot, int lane)
 {
+    if (!in_chain(C, pos, C.n)) return;
     const int node = C.c * C.n + pos;
     cp_async<4 * NP>(slot + lane * 4 * NP, buf + (size_t)node * C.KP2 + lane * NP);
     if (lane == 0) cp_async<4>(slot + 128 * NP, ofs + node);
@@ -317,6 +338,7 @@ template <int NP>
 __device__ __forceinline__ void store_msg(uint32_t* buf, int* ofs, const Ctx16& C, int pos,
                                           int lane, const uint32_t (&m)[NP], int off)
 {
+    if (!in_chain(C, pos, C.n)) return;
     uint32_t* p = buf + (size_t)(C.c * C.n + pos) * C.KP2 + lane * NP;
     if constexpr (NP == 1) p[0] = m[0];
     else if constexpr (NP == 2) *reinterpret_cast<uint2*>(p) = make_uint2(m[0], m[1]);
@@ -337,6 +359,7 @@ __device__ __forceinline__ void finalise(const Dmm16Args& A, const Ctx16& C, int
                                          int lin_off, const uint32_t (&rin)[NP], int rin_off,
                                          long long& lb_acc)
 {
+    if (!in_chain(C, k, C.n)) return;  // k is uniform over the warp
     const int pix = C.pix(k);
     uint32_t v[NP];
     uint32_t bad = 0;
@@ -654,6 +677,7 @@ __device__ __forceinline__ void chain16(const Dmm16Args& A, int chain, uint8_t* 
     C.c = chain;
     C.KP2 = 32 * NP;
     C.c16 = A.cost16 != nullptr;
+    C.err = A.err;
     const int n = C.n;
     const bool pad = PAD && (lane * 2 * NP >= A.L);
     long long lb_acc = 0;

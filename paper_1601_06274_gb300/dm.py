@@ -15,7 +15,9 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdm.so")
+# DM_CHECKED=1 selects the checked build (index checks in the kernels)
+LIB_PATH = os.path.join(_HERE, "libdm_checked.so" if os.environ.get("DM_CHECKED") == "1"
+                        else "libdm.so")
 
 DM_OK, DM_ERR_ARG, DM_ERR_CUDA, DM_ERR_RANGE, DM_ERR_TIMEOUT = 0, 1, 2, 3, 4
 DM_ERR_STATE, DM_ERR_WORKSPACE, DM_ERR_DEVICE = 5, 6, 7
