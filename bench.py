@@ -381,6 +381,12 @@ KERNEL_NAMES = {16: "dmm16_kernel", 32: "dmm_pass_kernel"}
 # changed since its capture has no entry and reports null
 NCU_TRAFFIC = {("kitti", "dmm16_kernel horizontal pass"): 351_392_000,
                ("kitti", "dmm16_kernel vertical pass"): 289_200_384}
+# smsp__inst_executed.sum per launch from the same capture: the pass is bound by
+# instruction issue, so its issue rate is reported beside the HBM roofline,
+# against 152 SMs x 4 schedulers x 1 warp-instruction per cycle at 2070 MHz
+NCU_INSTRUCTIONS = {("kitti", "dmm16_kernel horizontal pass"): 431_528_250,
+                    ("kitti", "dmm16_kernel vertical pass"): 404_710_668}
+ISSUE_PEAK_GINST_S = 152 * 4 * 2.070
 
 
 # ---------------------------------------------------------------------------
@@ -690,6 +696,14 @@ def main():
     avg = time_passes(ctx, d_left, d_right, NI, max(1, args.steps // 2), flush, stream)
     roofline = roofline_line(ctx, avg, H * W, L, 1, KERNEL_NAMES)
     roofline["traffic"] = NCU_TRAFFIC.get(("kitti", roofline["kernel"]))
+    inst = NCU_INSTRUCTIONS.get(("kitti", roofline["kernel"]))
+    if inst is not None:
+        dur = roofline["pass_ms"]["horizontal" if "horizontal" in roofline["kernel"] else "vertical"]
+        rate = inst / (dur / 1e3) / 1e9
+        roofline["issue"] = {"warp_instructions_per_launch": inst,
+                             "achieved_ginst_s": round(rate, 1),
+                             "peak_ginst_s": round(ISSUE_PEAK_GINST_S, 1),
+                             "frac": round(rate / ISSUE_PEAK_GINST_S, 4)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
