@@ -24,7 +24,7 @@ def test_api_walkthrough():
     u2 = ctx.solve(pair.left, pair.right, 10, 100)
     assert torch.equal(u, u2) and np.isfinite(ctx.energy())
 
-    out = dm.batch_solve([(pair.left, pair.right)], labels=[L])
+    out = dm.batch_solve([(pair.left, pair.right)], labels=[L], dmm_iters=10, pd_iters=100)
     assert torch.equal(out[0][0], u) and np.array_equal(out[0][1], labels)
 
     cost = torch.rand(H, W, L, device="cuda", requires_grad=True)
