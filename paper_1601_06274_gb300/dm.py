@@ -97,6 +97,9 @@ def lib() -> ctypes.CDLL:
             "dm_set_cost_volume_u16": [_vp, _vp, _vp, _vp, _i],
             "dm_cost_volume_warm": [_vp, _vp, _vp],
             "dm_solve_next": [_vp, _vp, _vp, _i, _i, _vp],
+            "dm_cost_volume_mirrored": [_vp, _vp, _vp],
+            "dm_lr_check": [_vp, _vp, _i, _i, ctypes.c_float, _vp, _vp, _vp, _vp],
+            "dm_solve_lr": [_vp, _vp, _vp, _vp, _i, _i, ctypes.c_float, _vp, _vp, _vp],
             "dm_set_data_weights": [_vp, _vp],
             "dm_set_lambda_r": [_vp, ctypes.c_double],
             "dm_tape_bytes": [_vp, _i, _i, ctypes.POINTER(ctypes.c_size_t)],
@@ -158,6 +161,9 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self._ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
         self._tape = None
+        # the workspace may be a block that work still queued on torch's stream
+        # writes (the caching allocator orders reuse on that stream only)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
         _ck(lib().dm_set_stream(self._h, _vp(self.stream.cuda_stream)), "dm_set_stream")
         _ck(lib().dm_bind_workspace(self._h, self._ws.data_ptr(), self.workspace_bytes),
             "dm_bind_workspace")
@@ -178,9 +184,23 @@ class Context:
     def _empty(self, shape, dtype):
         return self._torch.empty(shape, dtype=dtype, device=self.device)
 
+    def _fork(self):
+        # a context on its own stream reads what torch's stream produced
+        cur = self._torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+
+    def _join(self):
+        # ... and torch's stream reads what the context produced
+        cur = self._torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
+
     def _dev_u8(self, a):
         t = self._torch.as_tensor(np.ascontiguousarray(a)) if isinstance(a, np.ndarray) else a
-        return t.to(self.device, self._torch.uint8).contiguous()
+        t = t.to(self.device, self._torch.uint8).contiguous()
+        self._fork()
+        return t
 
     # -- entry points ------------------------------------------------------------
     def cost_volume(self, left, right):
@@ -203,6 +223,12 @@ class Context:
                                          self._wv.data_ptr(), int(cost_max)),
             "dm_set_cost_volume_u16")
 
+    def cost_volume_mirrored(self, left, right):
+        """The right view's problem of (left, right), in mirrored columns."""
+        self._left, self._right = self._dev_u8(left), self._dev_u8(right)
+        _ck(lib().dm_cost_volume_mirrored(self._h, self._left.data_ptr(), self._right.data_ptr()),
+            "dm_cost_volume_mirrored")
+
     def cost_volume_warm(self, left, right):
         self._left, self._right = self._dev_u8(left), self._dev_u8(right)
         _ck(lib().dm_cost_volume_warm(self._h, self._left.data_ptr(), self._right.data_ptr()),
@@ -211,8 +237,10 @@ class Context:
     def solve_next(self, left, right, dmm_iters: int, pd_iters: int, out=None):
         self._left, self._right = self._dev_u8(left), self._dev_u8(right)
         out = out if out is not None else self._empty((self.H, self.W), self._torch.float32)
+        self._fork()
         _ck(lib().dm_solve_next(self._h, self._left.data_ptr(), self._right.data_ptr(), dmm_iters,
                                 pd_iters, out.data_ptr()), "dm_solve_next")
+        self._join()
         return out
 
     def reset_duals(self):
@@ -238,8 +266,10 @@ class Context:
     def solve(self, left, right, dmm_iters: int, pd_iters: int, out=None):
         self._left, self._right = self._dev_u8(left), self._dev_u8(right)
         out = out if out is not None else self._empty((self.H, self.W), self._torch.float32)
+        self._fork()
         _ck(lib().dm_solve(self._h, self._left.data_ptr(), self._right.data_ptr(), dmm_iters,
                            pd_iters, out.data_ptr()), "dm_solve")
+        self._join()
         return out
 
     def solve_host(self, left, right, dmm_iters: int, pd_iters: int, u_out=None, labels_out=None):
@@ -254,18 +284,24 @@ class Context:
 
     def labels(self):
         out = self._empty((self.H, self.W), self._torch.int16)
+        self._fork()
         _ck(lib().dm_get_labels(self._h, out.data_ptr()), "dm_get_labels")
+        self._join()
         return out
 
     def disparity(self):
         out = self._empty((self.H, self.W), self._torch.float32)
+        self._fork()
         _ck(lib().dm_get_disparity(self._h, out.data_ptr()), "dm_get_disparity")
+        self._join()
         return out
 
     def duals(self):
         lh = self._empty((self.H, self.W, self.L), self._torch.int32)
         lv = self._empty((self.H, self.W, self.L), self._torch.int32)
+        self._fork()
         _ck(lib().dm_get_duals(self._h, lh.data_ptr(), lv.data_ptr()), "dm_get_duals")
+        self._join()
         return lh, lv
 
     def cost(self):
@@ -275,8 +311,10 @@ class Context:
         c = self._empty((self.H, self.W, self.L), dt)
         wh = self._empty((self.H, self.W), self._torch.uint8)
         wv = self._empty((self.H, self.W), self._torch.uint8)
+        self._fork()
         _ck(lib().dm_get_cost_volume(self._h, c.data_ptr(), wh.data_ptr(), wv.data_ptr()),
             "dm_get_cost_volume")
+        self._join()
         return c, wh, wv
 
     def lower_bounds(self, n: int):
@@ -433,6 +471,8 @@ class Batch:
         self.device = torch.device(device)
         self.stream = torch.cuda.Stream(self.device)   # capturable (not the legacy stream)
         self._ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+        # the block may still be written by work queued on torch's stream: bind after it
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
         _ck(lib().dm_batch_set_stream(self._h, _vp(self.stream.cuda_stream)), "dm_batch_set_stream")
         _ck(lib().dm_batch_bind_workspace(self._h, self._ws.data_ptr(), self.workspace_bytes),
             "dm_batch_bind_workspace")
@@ -472,7 +512,13 @@ class Batch:
         self._keep = (ls, rs, outs)
         _ck(lib().dm_batch_solve(self._h, self._ptrs(ls), self._ptrs(rs), dmm_iters, pd_iters,
                                  self._ptrs(outs)), "dm_batch_solve")
+        self._join()
         return outs
+
+    def _join(self):
+        # torch's stream continues after the batch's work: the outputs are ready for
+        # torch, and blocks the allocator hands out again are no longer in use
+        self._torch.cuda.current_stream(self.device).wait_stream(self.stream)
 
     def capture(self, lefts, rights, dmm_iters: int, pd_iters: int, outs):
         """Record one solve on these device buffers (torch tensors that stay
@@ -487,6 +533,7 @@ class Batch:
         (e.g. new inputs copied into the captured buffers)."""
         self.stream.wait_stream(self._torch.cuda.current_stream(self.device))
         _ck(lib().dm_batch_replay(self._h), "dm_batch_replay")
+        self._join()
 
     def sync(self):
         _ck(lib().dm_batch_sync(self._h), "dm_batch_sync")
@@ -496,6 +543,7 @@ class Batch:
         out = (ctypes.c_int * 5)()
         _ck(lib().dm_batch_tune(self._h, self._ptrs(ls), self._ptrs(rs),
                                 cache_path.encode() if cache_path else None, out), "dm_batch_tune")
+        self._join()
         return tuple(out)
 
     def set_tuning(self, choice):
@@ -510,6 +558,75 @@ class Batch:
         n = ctypes.c_uint64()
         _ck(lib().dm_batch_launch_count(self._h, ctypes.byref(n)), "dm_batch_launch_count")
         return n.value
+
+
+class StereoLR:
+    """Two views and the two-sided consistency check (dm_solve_lr): a context
+    per view, each on its own stream, so that the right view (the mirrored
+    pair) runs concurrently with the left one."""
+
+    def __init__(self, H: int, W: int, L: int, params: DmParams | None = None,
+                 device: str = "cuda"):
+        import torch
+        self._torch = torch
+        self.H, self.W, self.L = H, W, L
+        self.device = torch.device(device)
+        self.left = Context(H, W, L, params, device, stream=torch.cuda.Stream(self.device))
+        self.right = Context(H, W, L, params, device, stream=torch.cuda.Stream(self.device))
+
+    def outputs(self):
+        t = self._torch
+        return (t.empty((self.H, self.W), dtype=t.float32, device=self.device),
+                t.empty((self.H, self.W), dtype=t.uint8, device=self.device),
+                t.empty((self.H, self.W), dtype=t.float32, device=self.device))
+
+    def solve(self, left, right, dmm_iters: int, pd_iters: int, max_diff: float = 1.0,
+              outs=None):
+        """(u: checked left-view disparity, -1 where the check fails; ok: uint8
+        mask; u_right: the right view's disparity), float32 / uint8 [H, W]."""
+        torch = self._torch
+        cur = torch.cuda.current_stream(self.device)
+        lt, rt = self.left._dev_u8(left), self.left._dev_u8(right)
+        u, ok, ur = outs if outs is not None else self.outputs()
+        self._keep = (lt, rt, u, ok, ur)
+        self.left.stream.wait_stream(cur)        # inputs and outputs in torch's order
+        _ck(lib().dm_solve_lr(self.left._h, self.right._h, lt.data_ptr(), rt.data_ptr(),
+                              int(dmm_iters), int(pd_iters), float(max_diff), ok.data_ptr(),
+                              u.data_ptr(), _ptr(ur)), "dm_solve_lr")
+        cur.wait_stream(self.left.stream)        # the left stream joined the right one
+        return u, ok, ur
+
+    def sync(self):
+        self.left.sync()
+        self.right.sync()
+
+
+def lr_check(u_left, u_mirrored, max_diff: float = 1.0):
+    """dm_lr_check on torch's current stream: (u_out, ok, u_right) for a left-view
+    disparity and the disparity of the mirrored (right-view) problem."""
+    import torch
+    ul = u_left.contiguous()
+    um = u_mirrored.contiguous()
+    assert ul.dtype == torch.float32 and um.dtype == torch.float32 and ul.shape == um.shape
+    H, W = ul.shape
+    out = torch.empty_like(ul)
+    ur = torch.empty_like(ul)
+    ok = torch.empty((H, W), dtype=torch.uint8, device=ul.device)
+    st = torch.cuda.current_stream(ul.device).cuda_stream
+    _ck(lib().dm_lr_check(ul.data_ptr(), um.data_ptr(), H, W, float(max_diff), ok.data_ptr(),
+                          out.data_ptr(), ur.data_ptr(), _vp(st)), "dm_lr_check")
+    return out, ok, ur
+
+
+def solve_lr(left, right, L: int, dmm_iters: int = 10, pd_iters: int = 100,
+             max_diff: float = 1.0, params: DmParams | None = None, device: str = "cuda"):
+    """Both views of one pair and the consistency check: (u checked, ok, u_left,
+    u_right), the first three for the left view, -1 in u where the check fails."""
+    H, W = np.asarray(left).shape if isinstance(left, np.ndarray) else tuple(left.shape)
+    s = StereoLR(H, W, L, params, device)
+    u, ok, ur = s.solve(left, right, dmm_iters, pd_iters, max_diff)
+    s.sync()
+    return u, ok, s.left.disparity(), ur
 
 
 def discrete_pass_noalloc(params: DmParams, which: int, cost, wedge, lam_in, lam_out,

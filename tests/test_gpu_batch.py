@@ -54,6 +54,26 @@ def test_batch_matches_oracle(dm):
     _check_against_oracle(dm, b, pairs, SMALL, outs, 5, 50)
 
 
+def test_batch_after_work_still_queued_on_torch_stream(dm):
+    """A batch created while work of a freed context is still queued on torch's
+    stream: the caching allocator may hand the batch that context's memory, and
+    the batch binds it on its own stream only after the queued work."""
+    import torch
+    sp = S.make_pair(375, 1242, 128, planes=4, seed=3)
+    for _ in range(2):
+        ctx = dm.Context(375, 1242, 128)
+        ctx.solve(sp.left, sp.right, 10, 100)   # left running, not synchronised
+        del ctx
+        shapes = SMALL[:3]
+        pairs = _pairs(shapes, 500)
+        b = dm.Batch(shapes)
+        outs = b.solve([p.left for p in pairs], [p.right for p in pairs], 3, 20)
+        b.sync()
+        _check_against_oracle(dm, b, pairs, shapes, outs, 3, 20)
+        del b
+    torch.cuda.synchronize()
+
+
 def test_batch_graph_replays_new_inputs(dm):
     import torch
     shapes = SMALL[:6]
