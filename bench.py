@@ -38,11 +38,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="kitti", choices=["kitti", "diff", "stream", "batch"],
+    ap.add_argument("--workload", default="kitti", choices=["kitti", "diff", "stream", "batch", "lr"],
                     help="kitti: the plain method on the 1242x375x128 frame (default); "
                          "diff: forward + reverse mode of 200 PD iterations at 512x256x96; "
                          "stream: 60 warm-started frames of 1920x1080x256 (uint16 costs); "
-                         "batch: 32 pairs of mixed size and label count in one CUDA graph")
+                         "batch: 32 pairs of mixed size and label count in one CUDA graph; "
+                         "lr: both views of the 1242x375x128 frame and the consistency check")
     return ap.parse_args()
 
 
@@ -607,6 +608,149 @@ def run_batch(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+# ---------------------------------------------------------------------------
+# Two views and the consistency check at 1242x375x128
+# ---------------------------------------------------------------------------
+
+LR_METRIC = "Mpixel·labels/s (two views + consistency check) at 1242×375×128"
+# one launch of the check kernel per pixel: reads the left disparity and the
+# mirrored right disparity (2 x 4 B), writes the mask (1 B), the checked
+# disparity and the right view's disparity in its own columns (2 x 4 B)
+LR_CHECK_BYTES = 17
+
+
+def run_lr(args):
+    import numpy as np
+    import torch
+    from paper_1601_06274_gb300 import build, dm, synthetic as S
+    from oracle import oracle as O
+    build.build()
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    dev = torch.device("cuda", 0)
+    spec = S.KITTI
+    H, W, L = spec["H"], spec["W"], spec["L"]
+    NI, NP = spec["dmm_iters"], spec["pd_iters"]
+    sp = S.make_workload(spec, seed=0)
+    d_left = torch.from_numpy(sp.left).to(dev)
+    d_right = torch.from_numpy(sp.right).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    lr = dm.StereoLR(H, W, L)
+    outs = lr.outputs()
+    single = dm.Context(H, W, L)
+    d_u1 = torch.empty((H, W), dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        lr.solve(d_left, d_right, NI, NP, 1.0, outs)
+        single.solve(d_left, d_right, NI, NP, out=d_u1)
+    torch.cuda.synchronize()
+
+    def frames(fn, stream):
+        evs = []
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(k & 0xff)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                evs.append((a, b))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    # ---- timed region: K two-view frames (the right view on its own stream)
+    l0 = lr.left.launch_count() + lr.right.launch_count()
+    clk = Clocks(0)
+    ms = frames(lambda: lr.solve(d_left, d_right, NI, NP, 1.0, outs), lr.left.stream)
+    clocks = clk.stop()
+    launches = lr.left.launch_count() + lr.right.launch_count() - l0
+    lr.sync()
+    tot_ms = sum(ms)
+    units = H * W * L
+    value = job_value(units, args.steps, 1, tot_ms)
+    # the same frames through one view, for the cost of the second view and the check
+    ms1 = frames(lambda: single.solve(d_left, d_right, NI, NP, out=d_u1), single.stream)
+    single.sync()
+    u, ok, ur = outs
+    pass_frac = float(ok.float().mean())
+
+    # ---- end to end: pinned host images in, checked disparity and mask out
+    h_left = torch.from_numpy(sp.left).pin_memory()
+    h_right = torch.from_numpy(sp.right).pin_memory()
+    h_u = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    h_ok = torch.empty((H, W), dtype=torch.uint8).pin_memory()
+    cur = torch.cuda.current_stream(dev)
+    e_ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cur)
+        uu, oo, _ = lr.solve(h_left, h_right, NI, NP, 1.0, outs)
+        h_u.copy_(uu, non_blocking=True)
+        h_ok.copy_(oo, non_blocking=True)
+        b.record(cur)
+        torch.cuda.synchronize()
+        e_ms.append(a.elapsed_time(b))
+    e2e_value = units * args.steps / (sum(e_ms) / 1e3) / 1e6
+
+    # ---- the check kernel alone (HBM-bound), and the dominant Dual MM pass
+    ul = lr.left.disparity()
+    um = lr.right.disparity()
+    chk = []
+    for k in range(max(5, args.steps)):
+        flush.fill_(k & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cur)
+        dm.lr_check(ul, um, 1.0)
+        b.record(cur)
+        chk.append((a, b))
+    torch.cuda.synchronize()
+    chk_ms = sum(a.elapsed_time(b) for a, b in chk) / len(chk)
+    peak, src = hbm_peak()
+    chk_gbs = LR_CHECK_BYTES * H * W / (chk_ms / 1e3) / 1e9
+    avg = time_passes(single, d_left, d_right, NI, max(1, args.steps // 2), flush,
+                      single.stream)
+    roofline = roofline_line(single, avg, H * W, L, 1, KERNEL_NAMES)
+    roofline["traffic"] = NCU_TRAFFIC.get(("kitti", roofline["kernel"]))
+    roofline["check_kernel"] = {"kernel": "lr_check_kernel", "us": round(chk_ms * 1e3, 2),
+                                "bytes_per_launch": LR_CHECK_BYTES * H * W,
+                                "achieved_gbs": round(chk_gbs, 1),
+                                "frac": round(chk_gbs / peak, 4)}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        left_c, right_c, _ = cpu_sample()
+        O.lib()
+        t0 = time.perf_counter()
+        O.solve_lr(left_c, right_c, L, NI, NP, nthreads=os.cpu_count())
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": round(left_c.shape[0] * W * L / t_cpu / 1e6, 4), "unit": UNIT,
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"rows 0-{CPU_SAMPLE_ROWS - 1} ({W}x{CPU_SAMPLE_ROWS}x{L} crop) of the "
+                         f"frame, both views ({NI} Dual MM + {NP} PD iterations each) and the "
+                         f"check, {t_cpu:.2f} s"}
+
+    line = {
+        "metric": LR_METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(tot_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
+        "config": {"workload": "lr-1242x375x128", "H": H, "W": W, "L": L, "dmm_iters": NI,
+                   "pd_iters": NP, "max_diff": 1.0, "streams": 2,
+                   "l2": "flushed between steps (256 MB write, outside the timed events)",
+                   "parallelism": "replicas1"},
+        "single_view_ms": round(sum(ms1) / len(ms1), 4),
+        "two_view_over_single": round((tot_ms / args.steps) / (sum(ms1) / len(ms1)), 3),
+        "pass_fraction": round(pass_frac, 4),
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 2 * H * W,
+                "d2h_bytes_per_step": 5 * H * W},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -620,6 +764,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "lr":
+        run_lr(args)
         return
     import numpy as np
     import torch

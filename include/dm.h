@@ -183,6 +183,50 @@ DM_API int dm_solve(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, 
 DM_API int dm_solve_next(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right,
                          int dmm_iters, int pd_iters, float* d_u);
 
+/* ---- Two-sided consistency check (Sec. 4.1.1; Table 1's caption: the full
+ * left-right procedure takes twice the one-view time) ---------------------
+ *
+ * The right view's problem (the right image as reference, label l matching
+ * the left image's pixel x + l) is the left-reference problem of the mirrored
+ * pair: the right image with its columns reversed as reference, the left image
+ * with its columns reversed as the other view.  Its census cost volume is the
+ * right-view cost volume with columns reversed (the census bits of a mirrored
+ * window are a fixed permutation of the original ones, the same on both
+ * sides), so the unchanged kernels solve it. */
+
+/* dm_cost_volume of the mirrored pair built from (d_left, d_right), both
+ * H x W uint8 row-major on the device: the context then holds the right view's
+ * problem in mirrored columns, and its disparity u'[y][x'] is the right view's
+ * disparity at column W-1-x'.  Resets the duals. */
+DM_API int dm_cost_volume_mirrored(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right);
+
+/* The check itself, on caller buffers (device, H x W row-major):
+ * d_u_left: the left view's disparity (float32); d_u_mirrored: the mirrored
+ * problem's disparity.  The left pixel (y, x) with d = u_left[y][x] has its
+ * counterpart at xr = x - rint(d) (nearest, ties to even) and passes when
+ * 0 <= xr < W and |d - u_right[y][xr]| <= max_diff in single precision.
+ * Writes d_ok (uint8: 1 pass, 0 fail), d_u_out (float32: d, or -1 where the
+ * check fails) and, if not NULL, d_u_right (float32: the right view's
+ * disparity in its own columns).  Asynchronous on stream (NULL: the legacy
+ * default stream).  DM_ERR_ARG for a null buffer, H or W <= 0, or max_diff
+ * negative or not finite. */
+DM_API int dm_lr_check(const float* d_u_left, const float* d_u_mirrored, int H, int W,
+                       float max_diff, uint8_t* d_ok, float* d_u_out, float* d_u_right,
+                       void* stream);
+
+/* Both views and the check: `left` solves (d_left, d_right) as dm_solve does,
+ * `right` (another context of the same H, W, L and cost storage) solves the
+ * mirrored pair, then dm_lr_check writes d_ok, d_u and d_u_right (nullable)
+ * on the left context's stream.  When the two contexts have different streams
+ * the right view runs on its own stream, concurrently with the left view: it
+ * starts after the work queued on the left stream so far (the inputs), and
+ * the left stream waits for it before the check.  Each context keeps its own
+ * labels, duals and disparity for the getters.  DM_ERR_ARG for mismatched
+ * contexts (or the same context twice) and as dm_lr_check. */
+DM_API int dm_solve_lr(dm_ctx* left, dm_ctx* right, const uint8_t* d_left, const uint8_t* d_right,
+                       int dmm_iters, int pd_iters, float max_diff, uint8_t* d_ok, float* d_u,
+                       float* d_u_right);
+
 /* Same with host buffers: copies the images in and the disparity (and, if
  * h_labels is not NULL, the labels) out through the workspace; synchronous. */
 DM_API int dm_solve_host(dm_ctx* ctx, const uint8_t* h_left, const uint8_t* h_right,

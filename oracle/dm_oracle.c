@@ -111,6 +111,54 @@ int or_cost_volume(int H, int W, int L, const uint32_t* cl, const uint32_t* cr, 
     return OR_OK;
 }
 
+/* Right-view matching cost for the two-sided consistency check (Sec. 4.1.1
+ * names the check, the caption of Table 1 its doubled cost; reading R25): the
+ * right image is the reference, and its pixel x under label l is matched with
+ * the left image's pixel x + l:
+ * c[y][x][l] = Hamming(cR[y][x], cL[y][x+l]), or maxc if x + l >= W. */
+int or_cost_volume_right(int H, int W, int L, const uint32_t* cl, const uint32_t* cr, int maxc,
+                         int32_t* cost)
+{
+    if (H <= 0 || W <= 0 || L <= 0) return OR_ERR_ARG;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            for (int l = 0; l < L; ++l) {
+                int32_t v = maxc;
+                if (x + l < W) v = popcount32(cr[y * W + x] ^ cl[y * W + x + l]);
+                cost[((i64)y * W + x) * L + l] = v;
+            }
+    return OR_OK;
+}
+
+/* Two-sided consistency check (Sec. 4.1.1: the outliers that the truncated
+ * regulariser lets through are removed by checking the two views against each
+ * other; readings R26-R28).  The left pixel (y, x) with disparity d = ul[y][x]
+ * has its counterpart in the right view at xr = x - rint(d) (nearest integer,
+ * ties to even).  It passes when 0 <= xr < W and |d - ur[y][xr]| <= max_diff,
+ * the difference taken in single precision, the precision of the disparities.
+ * ok = 1 where it passes, else 0; out = d where it passes, else -1. */
+int or_lr_check(int H, int W, const float* ul, const float* ur, float max_diff, uint8_t* ok,
+                float* out)
+{
+    if (H <= 0 || W <= 0 || !(max_diff >= 0.0f)) return OR_ERR_ARG;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const i64 i = (i64)y * W + x;
+            const float d = ul[i];
+            int pass = 0;
+            if (isfinite(d) && fabsf(d) < 1.0e9f) {
+                const i64 xr = (i64)x - (i64)rintf(d);
+                if (xr >= 0 && xr < W) {
+                    const float diff = fabsf(d - ur[(i64)y * W + xr]);
+                    pass = diff <= max_diff;
+                }
+            }
+            ok[i] = (uint8_t)pass;
+            out[i] = pass ? d : -1.0f;
+        }
+    return OR_OK;
+}
+
 /* Edge strengths omega_ij (Sec. 2.1: image dependent, smaller across sharp
  * edges; reading R3).  wh[y][x] is the edge (y,x)-(y,x+1), wv[y][x] the edge
  * (y,x)-(y+1,x); entries without an edge are 0. */

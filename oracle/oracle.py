@@ -27,6 +27,7 @@ u32p = ctypes.POINTER(ctypes.c_uint32)
 u16p = ctypes.POINTER(ctypes.c_uint16)
 u8p = ctypes.POINTER(ctypes.c_uint8)
 f64p = ctypes.POINTER(ctypes.c_double)
+f32p = ctypes.POINTER(ctypes.c_float)
 
 
 class ContParams(ctypes.Structure):
@@ -55,6 +56,9 @@ def lib():
         L = _lib
         L.or_census.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int, u32p]
         L.or_cost_volume.argtypes = [ctypes.c_int] * 3 + [u32p, u32p, ctypes.c_int, i32p]
+        L.or_cost_volume_right.argtypes = [ctypes.c_int] * 3 + [u32p, u32p, ctypes.c_int, i32p]
+        L.or_lr_check.argtypes = [ctypes.c_int, ctypes.c_int, f32p, f32p, ctypes.c_float, u8p,
+                                  f32p]
         L.or_edge_weights.argtypes = [ctypes.c_int, ctypes.c_int, u8p] + [ctypes.c_int] * 3 + [i32p, i32p]
         L.or_r.argtypes = [ctypes.c_double] * 4
         L.or_r.restype = ctypes.c_double
@@ -149,6 +153,32 @@ def cost_volume(left: np.ndarray, right: np.ndarray, L: int, win: int = 5) -> np
     _chk(lib().or_cost_volume(H, W, L, _p(cl, u32p), _p(cr, u32p), win * win - 1,
                               _p(out, i32p)), "cost_volume")
     return out
+
+
+def cost_volume_right(left: np.ndarray, right: np.ndarray, L: int, win: int = 5) -> np.ndarray:
+    """Right-view cost volume (the right image as reference, matched l pixels to
+    the right in the left image), written from its definition."""
+    cl, cr = census(left, win), census(right, win)
+    H, W = cl.shape
+    out = np.zeros((H, W, L), dtype=np.int32)
+    _chk(lib().or_cost_volume_right(H, W, L, _p(cl, u32p), _p(cr, u32p), win * win - 1,
+                                    _p(out, i32p)), "cost_volume_right")
+    return out
+
+
+def lr_check(u_left: np.ndarray, u_right: np.ndarray, max_diff: float = 1.0):
+    """Two-sided consistency check of a left-view and a right-view disparity
+    (both float32 [H, W], each in its own view's coordinates); returns
+    (ok uint8 [H, W], checked disparity float32 [H, W], -1 where it fails)."""
+    ul = np.ascontiguousarray(u_left, dtype=np.float32)
+    ur = np.ascontiguousarray(u_right, dtype=np.float32)
+    assert ul.shape == ur.shape and ul.ndim == 2
+    H, W = ul.shape
+    ok = np.zeros((H, W), dtype=np.uint8)
+    out = np.zeros((H, W), dtype=np.float32)
+    _chk(lib().or_lr_check(H, W, _p(ul, f32p), _p(ur, f32p), float(max_diff), _p(ok, u8p),
+                           _p(out, f32p)), "lr_check")
+    return ok, out
 
 
 def edge_weights(img: np.ndarray, P: Params = Params()):
@@ -357,3 +387,20 @@ def solve(left, right, L: int, dmm_iters: int, pd_iters: int, P: Params = Params
                        labels.astype(np.float64), pd_iters, P)
     return dict(cost=cost, wh=wh, wv=wv, labels=labels, lb=lb, lam_h=lam_h, lam_v=lam_v, u=u,
                 state=st, energy=en)
+
+
+def solve_lr(left, right, L: int, dmm_iters: int, pd_iters: int, P: Params = Params(),
+             max_diff: float = 1.0, nthreads: int = 0):
+    """Two-view path with the consistency check (Sec. 4.1.1; readings R25-R28).
+    The left view is solve(left, right).  The right view is the same path on
+    the mirrored pair (mirrored right image as reference, mirrored left image
+    as the other view), whose cost volume is the right-view cost volume with
+    columns reversed; its disparity is mirrored back.  The check runs on the
+    two disparities rounded to float32."""
+    sl = solve(left, right, L, dmm_iters, pd_iters, P, nthreads)
+    sm = solve(np.ascontiguousarray(right[:, ::-1]), np.ascontiguousarray(left[:, ::-1]), L,
+               dmm_iters, pd_iters, P, nthreads)
+    u_left = sl["u"].astype(np.float32)
+    u_right = np.ascontiguousarray(sm["u"][:, ::-1]).astype(np.float32)
+    ok, out = lr_check(u_left, u_right, max_diff)
+    return dict(left=sl, mirrored=sm, u_left=u_left, u_right=u_right, ok=ok, u=out)

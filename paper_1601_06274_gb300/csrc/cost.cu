@@ -7,7 +7,10 @@
 //   clamp-to-edge indices.  Bit k is the k-th neighbour in raster order,
 //   centre skipped, set when I(neighbour) < I(centre).  The left image's
 //   threads also write the edge weights omega (Sec. 2.1: image dependent,
-//   weaker across intensity edges).
+//   weaker across intensity edges).  MIRROR computes the same for the mirrored
+//   pair (the right image, columns reversed, as the reference; the left image,
+//   columns reversed, as the other view): the right view's problem of the
+//   two-sided check (Sec. 4.1.1), with no extra pass over the images.
 // cost:   c[y][x][l] = popcount(cL[y][x] ^ cR[y][x-l]) or win*win-1 when
 //   x - l < 0.  One thread writes 16 consecutive labels of one pixel as a
 //   single 16-byte store, so a warp writes 512 contiguous bytes.
@@ -17,7 +20,7 @@
 namespace dm {
 namespace {
 
-template <int WIN>
+template <int WIN, bool MIRROR>
 __global__ void census_edges_kernel(const uint8_t* __restrict__ left,
                                     const uint8_t* __restrict__ right, int H, int W, int T,
                                     int w_hi, int w_lo, uint32_t* __restrict__ census,
@@ -27,9 +30,11 @@ __global__ void census_edges_kernel(const uint8_t* __restrict__ left,
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int img = blockIdx.z;
     if (x >= W || y >= H) return;
-    const uint8_t* I = img == 0 ? left : right;
+    // column xx of the (possibly mirrored) image: I[row + col(xx)]
+    const uint8_t* I = (img == 0) != MIRROR ? left : right;
+    auto col = [W](int xx) { return MIRROR ? W - 1 - xx : xx; };
     constexpr int r = WIN / 2;
-    const int centre = I[y * W + x];
+    const int centre = I[y * W + col(x)];
     uint32_t code = 0;
     int bit = 0;
 #pragma unroll
@@ -39,7 +44,7 @@ __global__ void census_edges_kernel(const uint8_t* __restrict__ left,
         for (int dx = -r; dx <= r; ++dx) {
             if (dy == 0 && dx == 0) continue;
             const int xx = min(max(x + dx, 0), W - 1);
-            code |= (uint32_t)(I[yy * W + xx] < centre) << bit;
+            code |= (uint32_t)(I[yy * W + col(xx)] < centre) << bit;
             ++bit;
         }
     }
@@ -47,8 +52,8 @@ __global__ void census_edges_kernel(const uint8_t* __restrict__ left,
     if (img == 0) {
         const size_t i = (size_t)y * W + x;
         uint8_t a = 0, b = 0;
-        if (x + 1 < W) a = (uint8_t)(abs(centre - (int)I[i + 1]) < T ? w_hi : w_lo);
-        if (y + 1 < H) b = (uint8_t)(abs(centre - (int)I[i + W]) < T ? w_hi : w_lo);
+        if (x + 1 < W) a = (uint8_t)(abs(centre - (int)I[y * W + col(x + 1)]) < T ? w_hi : w_lo);
+        if (y + 1 < H) b = (uint8_t)(abs(centre - (int)I[(y + 1) * W + col(x)]) < T ? w_hi : w_lo);
         wh[i] = a;
         wv[i] = b;
     }
@@ -106,14 +111,13 @@ __global__ void cost_kernel(const uint32_t* __restrict__ cl, const uint32_t* __r
 
 cudaError_t launch_census_edges(const uint8_t* left, const uint8_t* right, int H, int W, int win,
                                 int T, int w_hi, int w_lo, uint32_t* census, uint8_t* wh,
-                                uint8_t* wv, cudaStream_t s)
+                                uint8_t* wv, bool mirror, cudaStream_t s)
 {
     dim3 blk(32, 8);
     dim3 grd((W + 31) / 32, (H + 7) / 8, 2);
-    if (win == 5)
-        census_edges_kernel<5><<<grd, blk, 0, s>>>(left, right, H, W, T, w_hi, w_lo, census, wh, wv);
-    else
-        census_edges_kernel<3><<<grd, blk, 0, s>>>(left, right, H, W, T, w_hi, w_lo, census, wh, wv);
+    auto k = win == 5 ? (mirror ? census_edges_kernel<5, true> : census_edges_kernel<5, false>)
+                      : (mirror ? census_edges_kernel<3, true> : census_edges_kernel<3, false>);
+    k<<<grd, blk, 0, s>>>(left, right, H, W, T, w_hi, w_lo, census, wh, wv);
     return cudaGetLastError();
 }
 

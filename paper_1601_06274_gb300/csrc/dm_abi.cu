@@ -364,14 +364,14 @@ int run_pass(dm_ctx* c, int which, uint16_t* labels, long long* lb)
 }
 
 // census, edge weights and cost volume of a new pair (the duals are left alone)
-int census_cost(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right)
+int census_cost(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, bool mirror = false)
 {
     uint8_t* ws = ctx->ws;
     uint32_t* census = reinterpret_cast<uint32_t*>(ws + ctx->lay.census);
     const int maxc = ctx->p.census_win * ctx->p.census_win - 1;
     DM_CK(dm::launch_census_edges(d_left, d_right, ctx->H, ctx->W, ctx->p.census_win,
                                   ctx->p.edge_threshold, ctx->p.w_hi, ctx->p.w_lo, census,
-                                  ws + ctx->lay.wh, ws + ctx->lay.wv, ctx->stream));
+                                  ws + ctx->lay.wh, ws + ctx->lay.wv, mirror, ctx->stream));
     DM_CK(dm::launch_cost(census, ctx->H, ctx->W, ctx->L, maxc, ws + ctx->lay.cost,
                           ctx->cost_bytes, ctx->stream));
     ctx->launches += 2;
@@ -523,6 +523,10 @@ DM_API int dm_create(int H, int W, int L, const dm_params* p, dm_ctx** out)
 
 DM_API int dm_destroy(dm_ctx* ctx)
 {
+    if (ctx != nullptr) {
+        if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+        if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    }
     delete ctx;
     return DM_OK;
 }
@@ -1200,6 +1204,71 @@ DM_API int dm_solve_next(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_ri
     if ((rc = dm_discrete(ctx, dmm_iters, nullptr))) return rc;
     if ((rc = dm_refine(ctx, pd_iters, nullptr))) return rc;
     if (d_u != nullptr && (rc = dm_get_disparity(ctx, d_u))) return rc;
+    return DM_OK;
+}
+
+DM_API int dm_cost_volume_mirrored(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right)
+{
+    const Range range("dm_cost_volume_mirrored");
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (d_left == nullptr || d_right == nullptr) return DM_ERR_ARG;
+    if ((rc = census_cost(ctx, d_left, d_right, true))) return rc;
+    return dm_reset_duals(ctx);
+}
+
+DM_API int dm_lr_check(const float* d_u_left, const float* d_u_mirrored, int H, int W,
+                       float max_diff, uint8_t* d_ok, float* d_u_out, float* d_u_right,
+                       void* stream)
+{
+    if (d_u_left == nullptr || d_u_mirrored == nullptr || d_ok == nullptr || d_u_out == nullptr)
+        return DM_ERR_ARG;
+    if (H <= 0 || W <= 0 || (long long)H * W > (1LL << 31) || !(max_diff >= 0.0f) ||
+        !std::isfinite(max_diff))
+        return DM_ERR_ARG;
+    DM_CK(dm::launch_lr_check(d_u_left, d_u_mirrored, H, W, max_diff, d_ok, d_u_out, d_u_right,
+                              static_cast<cudaStream_t>(stream)));
+    return DM_OK;
+}
+
+DM_API int dm_solve_lr(dm_ctx* left, dm_ctx* right, const uint8_t* d_left, const uint8_t* d_right,
+                       int dmm_iters, int pd_iters, float max_diff, uint8_t* d_ok, float* d_u,
+                       float* d_u_right)
+{
+    const Range range("dm_solve_lr");
+    int rc;
+    if ((rc = ready(left)) || (rc = ready(right))) return rc;
+    if (left == right || left->H != right->H || left->W != right->W || left->L != right->L ||
+        left->cost_bytes != right->cost_bytes)
+        return DM_ERR_ARG;
+    if (d_left == nullptr || d_right == nullptr || d_ok == nullptr || d_u == nullptr)
+        return DM_ERR_ARG;
+    if (!(max_diff >= 0.0f) || !std::isfinite(max_diff)) return DM_ERR_ARG;
+    const bool fork = left->stream != right->stream;
+    if (fork) {
+        if (left->ev_fork == nullptr)
+            DM_CK(cudaEventCreateWithFlags(&left->ev_fork, cudaEventDisableTiming));
+        if (left->ev_join == nullptr)
+            DM_CK(cudaEventCreateWithFlags(&left->ev_join, cudaEventDisableTiming));
+        // the inputs are ready in the left stream's order
+        DM_CK(cudaEventRecord(left->ev_fork, left->stream));
+        DM_CK(cudaStreamWaitEvent(right->stream, left->ev_fork, 0));
+    }
+    // right view: the mirrored pair through the unchanged path, on its own stream
+    if ((rc = dm_cost_volume_mirrored(right, d_left, d_right))) return rc;
+    if ((rc = dm_discrete(right, dmm_iters, nullptr))) return rc;
+    if ((rc = dm_refine(right, pd_iters, nullptr))) return rc;
+    // left view, concurrently when the streams differ
+    if ((rc = dm_solve(left, d_left, d_right, dmm_iters, pd_iters, nullptr))) return rc;
+    if (fork) {
+        DM_CK(cudaEventRecord(left->ev_join, right->stream));
+        DM_CK(cudaStreamWaitEvent(left->stream, left->ev_join, 0));
+    }
+    const dm::PdArgs al = pd_args(left);
+    const dm::PdArgs ar = pd_args(right);
+    DM_CK(dm::launch_lr_check(al.u, ar.u, left->H, left->W, max_diff, d_ok, d_u, d_u_right,
+                              left->stream));
+    left->launches += 1;
     return DM_OK;
 }
 

@@ -43,6 +43,9 @@ struct dm_ctx {
     size_t tape_bytes = 0;
     int tape_iters = 0, tape_ckpt = 0;
     bool tape_valid = false;
+    // two-view solve: fork to the right view's stream and join back (created on
+    // first use, destroyed by dm_destroy)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace dm {

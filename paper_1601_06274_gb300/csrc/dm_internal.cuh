@@ -209,9 +209,14 @@ int penalty_taps(int omega, int L, const dm_params& p, int32_t* row);
 // cost.cu
 cudaError_t launch_census_edges(const uint8_t* left, const uint8_t* right, int H, int W, int win,
                                 int T, int w_hi, int w_lo, uint32_t* census, uint8_t* wh,
-                                uint8_t* wv, cudaStream_t s);
+                                uint8_t* wv, bool mirror, cudaStream_t s);
 cudaError_t launch_cost(const uint32_t* census, int H, int W, int L, int maxc, void* cost,
                         int cost_bytes, cudaStream_t s);
+
+// lr.cu: two-sided consistency check of a left-view disparity and the
+// disparity of the mirrored (right-view) problem
+cudaError_t launch_lr_check(const float* ul, const float* um, int H, int W, float max_diff,
+                            uint8_t* ok, float* out, float* ur, cudaStream_t s);
 
 // dmm.cu
 cudaError_t launch_dmm_pass(const DmmArgs& a, int lpt, int radius, cudaStream_t s);

@@ -176,3 +176,30 @@ def test_batch_create_and_workspace_without_gpu(lib):
     b2 = ctypes.c_void_p()
     assert lib.dm_batch_create(n, bad_H, W, L, ctypes.byref(p), ctypes.byref(b2)) == dm.DM_ERR_ARG
     assert lib.dm_batch_destroy(b) == 0
+
+
+def test_two_view_calls_check_arguments_without_gpu(lib):
+    from paper_1601_06274_gb300 import dm
+    p = dm.default_params()
+    a, b = ctypes.c_void_p(), ctypes.c_void_p()
+    assert lib.dm_create(8, 8, 16, ctypes.byref(p), ctypes.byref(a)) == 0
+    assert lib.dm_create(8, 8, 16, ctypes.byref(p), ctypes.byref(b)) == 0
+    fake = ctypes.c_void_p(4096)
+    # no workspace bound yet: state errors, before anything reaches the device
+    assert lib.dm_cost_volume_mirrored(a, fake, fake) == dm.DM_ERR_STATE
+    assert lib.dm_solve_lr(a, b, fake, fake, 1, 1, 1.0, fake, fake, None) == dm.DM_ERR_STATE
+    assert lib.dm_solve_lr(None, b, fake, fake, 1, 1, 1.0, fake, fake, None) == dm.DM_ERR_ARG
+    # the check's arguments are validated on the host
+    for H, W, md, ptrs in [(0, 4, 1.0, (fake, fake, fake, fake)),
+                           (4, -1, 1.0, (fake, fake, fake, fake)),
+                           (4, 4, -0.5, (fake, fake, fake, fake)),
+                           (4, 4, float("nan"), (fake, fake, fake, fake)),
+                           (4, 4, float("inf"), (fake, fake, fake, fake)),
+                           (4, 4, 1.0, (None, fake, fake, fake)),
+                           (4, 4, 1.0, (fake, None, fake, fake)),
+                           (4, 4, 1.0, (fake, fake, None, fake)),
+                           (4, 4, 1.0, (fake, fake, fake, None))]:
+        ul, um, ok, out = ptrs
+        assert lib.dm_lr_check(ul, um, H, W, md, ok, out, None, None) == dm.DM_ERR_ARG
+    lib.dm_destroy(a)
+    lib.dm_destroy(b)
