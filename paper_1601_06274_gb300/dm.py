@@ -601,17 +601,20 @@ class StereoLR:
         self.right.sync()
 
 
-def lr_check(u_left, u_mirrored, max_diff: float = 1.0):
+def lr_check(u_left, u_mirrored, max_diff: float = 1.0, outs=None):
     """dm_lr_check on torch's current stream: (u_out, ok, u_right) for a left-view
-    disparity and the disparity of the mirrored (right-view) problem."""
+    disparity and the disparity of the mirrored (right-view) problem; outs:
+    optional preallocated (u_out, ok, u_right)."""
     import torch
     ul = u_left.contiguous()
     um = u_mirrored.contiguous()
     assert ul.dtype == torch.float32 and um.dtype == torch.float32 and ul.shape == um.shape
     H, W = ul.shape
-    out = torch.empty_like(ul)
-    ur = torch.empty_like(ul)
-    ok = torch.empty((H, W), dtype=torch.uint8, device=ul.device)
+    if outs is None:
+        outs = (torch.empty_like(ul), torch.empty((H, W), dtype=torch.uint8, device=ul.device),
+                torch.empty_like(ul))
+    out, ok, ur = outs
+    assert out.shape == ok.shape == ur.shape == (H, W) and ok.dtype == torch.uint8
     st = torch.cuda.current_stream(ul.device).cuda_stream
     _ck(lib().dm_lr_check(ul.data_ptr(), um.data_ptr(), H, W, float(max_diff), ok.data_ptr(),
                           out.data_ptr(), ur.data_ptr(), _vp(st)), "dm_lr_check")

@@ -34,7 +34,7 @@ def dm():
 
 
 def _mirror(a):
-    return np.ascontiguousarray(a[:, ::-1])
+    return a[:, ::-1].copy()
 
 
 def _np(t):
@@ -169,7 +169,7 @@ def test_solve_lr_full_frame(dm):
     import torch
     spec = S.KITTI
     pair = S.make_workload(spec, seed=0)
-    H, W, L = spec.H, spec.W, spec.L
+    H, W, L = spec["H"], spec["W"], spec["L"]
     s = dm.StereoLR(H, W, L)
     u, ok, ur = s.solve(pair.left, pair.right, 10, 100, 1.0)
     s.sync()
