@@ -307,6 +307,76 @@ void or_hier_minorant(int n, int K, const i64* theta, const i64* V, i64* lam)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Other minorants of a chain (Sec. 2.3 "Good and Fast Minorants"; App. A).  */
+/* ------------------------------------------------------------------------ */
+
+/* floor(a / d) for d > 0 */
+static i64 floor_div(i64 a, i64 d) { return a >= 0 ? a / d : -((-a + d - 1) / d); }
+
+/* Naive minorant: every node takes its min-marginal of the chain divided by
+ * the chain length n (reading R29: rounded down, so that the sum over the
+ * nodes stays below f). */
+void or_naive_minorant(int n, int K, const i64* theta, const i64* V, i64* lam)
+{
+    or_min_marginals(n, K, theta, V, lam);
+    for (i64 e = 0; e < (i64)n * K; ++e) lam[e] = floor_div(lam[e], n);
+}
+
+/* Iterative minorant (Alg. iterative-minorant; reading R30).  lam starts at 0.
+ * Pass s = 1..max_pass visits the nodes forward (s odd) or backward (s even);
+ * at node i the min-marginal of the remainder f - lam is the message entering
+ * i from the side visited earlier in this pass (Eq. msg-pass, formed with the
+ * nodes already updated), plus theta_i - lam_i, plus the message entering from
+ * the other side, left by the previous pass (an initial backward sweep before
+ * the first pass); then lam_i += floor(gamma_s m_i), gamma_s = gn/gd for
+ * s < max_pass and 1 for the last pass. */
+int or_iterative_minorant(int n, int K, const i64* theta, const i64* V, int max_pass, int gn,
+                          int gd, i64* lam)
+{
+    if (n <= 0 || K <= 0 || max_pass < 1 || gn < 0 || gd <= 0 || gn > gd) return OR_ERR_ARG;
+    i64* left = (i64*)calloc((size_t)n * K, sizeof(i64));   /* left[i]: message (i-1 -> i)  */
+    i64* right = (i64*)calloc((size_t)n * K, sizeof(i64));  /* right[i]: message (i+1 -> i) */
+    i64* tmp = (i64*)malloc((size_t)K * sizeof(i64));
+    memset(lam, 0, (size_t)n * K * sizeof(i64));
+    for (int k = n - 2; k >= 0; --k) {
+        for (int l = 0; l < K; ++l)
+            tmp[l] = theta[(i64)(k + 1) * K + l] - lam[(i64)(k + 1) * K + l] + right[(i64)(k + 1) * K + l];
+        or_msg(K, tmp, V + (i64)k * K, right + (i64)k * K);
+    }
+    for (int s = 1; s <= max_pass; ++s) {
+        const i64 num = s == max_pass ? 1 : gn, den = s == max_pass ? 1 : gd;
+        const int fwd = (s & 1) == 1;
+        for (int t = 0; t < n; ++t) {
+            const int i = fwd ? t : n - 1 - t;
+            if (fwd) {
+                if (i == 0) memset(left, 0, (size_t)K * sizeof(i64));
+                else {
+                    for (int l = 0; l < K; ++l)
+                        tmp[l] = theta[(i64)(i - 1) * K + l] - lam[(i64)(i - 1) * K + l] +
+                                 left[(i64)(i - 1) * K + l];
+                    or_msg(K, tmp, V + (i64)(i - 1) * K, left + (i64)i * K);
+                }
+            } else {
+                if (i == n - 1) memset(right + (i64)(n - 1) * K, 0, (size_t)K * sizeof(i64));
+                else {
+                    for (int l = 0; l < K; ++l)
+                        tmp[l] = theta[(i64)(i + 1) * K + l] - lam[(i64)(i + 1) * K + l] +
+                                 right[(i64)(i + 1) * K + l];
+                    or_msg(K, tmp, V + (i64)i * K, right + (i64)i * K);
+                }
+            }
+            for (int l = 0; l < K; ++l) {
+                const i64 e = (i64)i * K + l;
+                const i64 m = left[e] + theta[e] - lam[e] + right[e];
+                lam[e] += floor_div(m * num, den);
+            }
+        }
+    }
+    free(left); free(right); free(tmp);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Dual MM (Alg. Dual_MM) on the 4-connected grid split into horizontal      */
 /* chains f (data cost + horizontal edges) and vertical chains g (vertical    */
 /* edges only).  lam_h is the minorant f^{k+1} of f, lam_v the minorant g^k.  */
@@ -340,14 +410,18 @@ static void free_tables(or_tables* T)
 
 /* One pass of Alg. Dual_MM.
  *   which = 0 (horizontal): theta = cost + lam_in (lam_in = lam_v),
- *             mu = hier(theta), lam_out = mu - lam_in   (steps 1-2)
+ *             mu = minorant(theta), lam_out = mu - lam_in   (steps 1-2)
  *   which = 1 (vertical):   theta = lam_in (lam_in = lam_h),
- *             nu = hier(theta), lam_out = nu - lam_in   (steps 3-4)     */
-int or_dmm_pass(int H, int W, int L, const int32_t* cost, const int32_t* wh,
-                const int32_t* wv, double eps, double delta, double C, int which,
-                const i64* lam_in, i64* lam_out, int nthreads)
+ *             nu = minorant(theta), lam_out = nu - lam_in   (steps 3-4)
+ * kind: 0 hierarchical (App. A), 1 naive, 2 iterative (max_pass, gn/gd). */
+int or_dmm_pass_kind(int H, int W, int L, const int32_t* cost, const int32_t* wh,
+                     const int32_t* wv, double eps, double delta, double C, int which,
+                     const i64* lam_in, i64* lam_out, int nthreads, int kind, int max_pass,
+                     int gn, int gd)
 {
     if (H <= 0 || W <= 0 || L <= 0 || (which != 0 && which != 1)) return OR_ERR_ARG;
+    if (kind < 0 || kind > 2) return OR_ERR_ARG;
+    if (kind == 2 && (max_pass < 1 || gn < 0 || gd <= 0 || gn > gd)) return OR_ERR_ARG;
     or_tables T;
     int rc = build_tables(&T, L, which == 0 ? wh : wv, H * W, eps, delta, C);
     if (rc) { free_tables(&T); return rc; }
@@ -374,7 +448,9 @@ int or_dmm_pass(int H, int W, int L, const int32_t* cost, const int32_t* wh,
                 memcpy(V + (i64)k * L, tab, (size_t)L * sizeof(i64));
             }
         }
-        or_hier_minorant(n, L, theta, V, mu);
+        if (kind == 0) or_hier_minorant(n, L, theta, V, mu);
+        else if (kind == 1) or_naive_minorant(n, L, theta, V, mu);
+        else or_iterative_minorant(n, L, theta, V, max_pass, gn, gd, mu);
         for (int k = 0; k < n; ++k) {
             int y = which == 0 ? c : k, x = which == 0 ? k : c;
             i64 pix = (i64)y * W + x;
@@ -385,6 +461,14 @@ int or_dmm_pass(int H, int W, int L, const int32_t* cost, const int32_t* wh,
     }
     free_tables(&T);
     return OR_OK;
+}
+
+int or_dmm_pass(int H, int W, int L, const int32_t* cost, const int32_t* wh,
+                const int32_t* wv, double eps, double delta, double C, int which,
+                const i64* lam_in, i64* lam_out, int nthreads)
+{
+    return or_dmm_pass_kind(H, W, L, cost, wh, wv, eps, delta, C, which, lam_in, lam_out,
+                            nthreads, 0, 1, 1, 1);
 }
 
 /* Labels and lower bound from the two minorants (weak duality, Eq. DD-dual;
@@ -407,19 +491,30 @@ i64 or_dmm_outputs(int H, int W, int L, const i64* lam_h, const i64* lam_v, uint
 
 /* Full Dual MM: iters x (horizontal pass, vertical pass), starting from the
  * given lam_v (zero for a cold start).  lb[t] is the bound after iteration t. */
-int or_dmm(int H, int W, int L, const int32_t* cost, const int32_t* wh, const int32_t* wv,
-           double eps, double delta, double C, int iters, i64* lam_h, i64* lam_v, i64* lb,
-           uint16_t* labels, int nthreads)
+int or_dmm_kind(int H, int W, int L, const int32_t* cost, const int32_t* wh,
+                const int32_t* wv, double eps, double delta, double C, int iters, i64* lam_h,
+                i64* lam_v, i64* lb, uint16_t* labels, int nthreads, int kind, int max_pass,
+                int gn, int gd)
 {
     for (int t = 0; t < iters; ++t) {
-        int rc = or_dmm_pass(H, W, L, cost, wh, wv, eps, delta, C, 0, lam_v, lam_h, nthreads);
+        int rc = or_dmm_pass_kind(H, W, L, cost, wh, wv, eps, delta, C, 0, lam_v, lam_h,
+                                  nthreads, kind, max_pass, gn, gd);
         if (rc) return rc;
-        rc = or_dmm_pass(H, W, L, cost, wh, wv, eps, delta, C, 1, lam_h, lam_v, nthreads);
+        rc = or_dmm_pass_kind(H, W, L, cost, wh, wv, eps, delta, C, 1, lam_h, lam_v, nthreads,
+                              kind, max_pass, gn, gd);
         if (rc) return rc;
         i64 b = or_dmm_outputs(H, W, L, lam_h, lam_v, (t == iters - 1) ? labels : NULL);
         if (lb) lb[t] = b;
     }
     return OR_OK;
+}
+
+int or_dmm(int H, int W, int L, const int32_t* cost, const int32_t* wh, const int32_t* wv,
+           double eps, double delta, double C, int iters, i64* lam_h, i64* lam_v, i64* lb,
+           uint16_t* labels, int nthreads)
+{
+    return or_dmm_kind(H, W, L, cost, wh, wv, eps, delta, C, iters, lam_h, lam_v, lb, labels,
+                       nthreads, 0, 1, 1, 1);
 }
 
 /* Discrete energy, Eq. (energy-pairwise) with the stereo terms of Sec. 2.2. */

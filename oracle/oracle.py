@@ -69,6 +69,14 @@ def lib():
         L.or_msg.argtypes = [ctypes.c_int, i64p, i64p, i64p]
         L.or_min_marginals.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
         L.or_hier_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
+        L.or_naive_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
+        L.or_iterative_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p] + \
+            [ctypes.c_int] * 3 + [i64p]
+        L.or_dmm_pass_kind.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p]
+                                       + [ctypes.c_double] * 3 + [ctypes.c_int, i64p, i64p]
+                                       + [ctypes.c_int] * 5)
+        L.or_dmm_kind.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
+                                  + [ctypes.c_int, i64p, i64p, i64p, u16p] + [ctypes.c_int] * 5)
         L.or_dmm_pass.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
                                   + [ctypes.c_int, i64p, i64p, ctypes.c_int])
         L.or_dmm_outputs.argtypes = [ctypes.c_int] * 3 + [i64p, i64p, u16p]
@@ -228,14 +236,47 @@ def hier_minorant(theta: np.ndarray, V: np.ndarray) -> np.ndarray:
     return out
 
 
-def dmm_pass(cost, wh, wv, which: int, lam_in, P: Params = Params(), nthreads: int = 0):
+def _chain_args(theta, V):
+    theta = np.ascontiguousarray(theta, dtype=np.int64)
+    n, K = theta.shape
+    V = np.ascontiguousarray(V, dtype=np.int64).reshape(max(n - 1, 1), K) if n > 1 else np.zeros((1, K), np.int64)
+    return theta, V, n, K
+
+
+def naive_minorant(theta: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """floor(min-marginal / n) at every node of the chain (theta [n, K], V [n-1, K])."""
+    theta, V, n, K = _chain_args(theta, V)
+    out = np.zeros_like(theta)
+    lib().or_naive_minorant(n, K, _p(theta, i64p), _p(V, i64p), _p(out, i64p))
+    return out
+
+
+def iterative_minorant(theta: np.ndarray, V: np.ndarray, max_pass: int = 3,
+                       gamma=(1, 4)) -> np.ndarray:
+    """Alg. iterative-minorant with gamma = gamma[0] / gamma[1] (1 on the last pass)."""
+    theta, V, n, K = _chain_args(theta, V)
+    out = np.zeros_like(theta)
+    _chk(lib().or_iterative_minorant(n, K, _p(theta, i64p), _p(V, i64p), int(max_pass),
+                                     int(gamma[0]), int(gamma[1]), _p(out, i64p)),
+         "iterative_minorant")
+    return out
+
+
+MINORANTS = {"hier": 0, "naive": 1, "iterative": 2}
+
+
+def dmm_pass(cost, wh, wv, which: int, lam_in, P: Params = Params(), nthreads: int = 0,
+             minorant: str = "hier", max_pass: int = 3, gamma=(1, 4)):
     cost = np.ascontiguousarray(cost, dtype=np.int32)
     H, W, L = cost.shape
     lam_in = np.ascontiguousarray(lam_in, dtype=np.int64)
     out = np.zeros((H, W, L), dtype=np.int64)
-    _chk(lib().or_dmm_pass(H, W, L, _p(cost, i32p), _p(np.ascontiguousarray(wh, np.int32), i32p),
-                           _p(np.ascontiguousarray(wv, np.int32), i32p), P.eps, P.delta, P.C,
-                           which, _p(lam_in, i64p), _p(out, i64p), nthreads), "dmm_pass")
+    _chk(lib().or_dmm_pass_kind(H, W, L, _p(cost, i32p),
+                                _p(np.ascontiguousarray(wh, np.int32), i32p),
+                                _p(np.ascontiguousarray(wv, np.int32), i32p), P.eps, P.delta, P.C,
+                                which, _p(lam_in, i64p), _p(out, i64p), nthreads,
+                                MINORANTS[minorant], int(max_pass), int(gamma[0]),
+                                int(gamma[1])), "dmm_pass")
     return out
 
 
@@ -248,18 +289,21 @@ def dmm_outputs(lam_h, lam_v):
     return labels, int(lb)
 
 
-def dmm(cost, wh, wv, iters: int, P: Params = Params(), lam_v0=None, nthreads: int = 0):
-    """Dual MM; returns (labels, lb per iteration, lam_h, lam_v)."""
+def dmm(cost, wh, wv, iters: int, P: Params = Params(), lam_v0=None, nthreads: int = 0,
+        minorant: str = "hier", max_pass: int = 3, gamma=(1, 4)):
+    """Dual MM with the chosen chain minorant; returns (labels, lb per
+    iteration, lam_h, lam_v)."""
     cost = np.ascontiguousarray(cost, dtype=np.int32)
     H, W, L = cost.shape
     lam_h = np.zeros((H, W, L), dtype=np.int64)
     lam_v = np.zeros((H, W, L), dtype=np.int64) if lam_v0 is None else np.array(lam_v0, dtype=np.int64)
     lb = np.zeros(max(iters, 1), dtype=np.int64)
     labels = np.zeros((H, W), dtype=np.uint16)
-    _chk(lib().or_dmm(H, W, L, _p(cost, i32p), _p(np.ascontiguousarray(wh, np.int32), i32p),
-                      _p(np.ascontiguousarray(wv, np.int32), i32p), P.eps, P.delta, P.C, iters,
-                      _p(lam_h, i64p), _p(lam_v, i64p), _p(lb, i64p), _p(labels, u16p),
-                      nthreads), "dmm")
+    _chk(lib().or_dmm_kind(H, W, L, _p(cost, i32p), _p(np.ascontiguousarray(wh, np.int32), i32p),
+                           _p(np.ascontiguousarray(wv, np.int32), i32p), P.eps, P.delta, P.C,
+                           iters, _p(lam_h, i64p), _p(lam_v, i64p), _p(lb, i64p),
+                           _p(labels, u16p), nthreads, MINORANTS[minorant], int(max_pass),
+                           int(gamma[0]), int(gamma[1])), "dmm")
     return labels, lb[:iters], lam_h, lam_v
 
 
