@@ -404,6 +404,30 @@ DM_API int dm_discrete_pass_noalloc(int H, int W, int L, const dm_params* p, int
                                     const int32_t* d_lam_in, int32_t* d_lam_out,
                                     int32_t* d_err, void* stream);
 
+/* ---- Chain minorant of the Dual MM passes (Sec. 2.3 "Good and Fast
+ * Minorants"; App. A) ------------------------------------------------------
+ *
+ * DM_MINORANT_HIER (the default): the hierarchical minorant of Alg. Handshake.
+ * DM_MINORANT_NAIVE: every node of a chain takes its min-marginal m_i divided
+ *   by the chain length n, rounded down: floor(m_i / n).
+ * DM_MINORANT_ITERATIVE (Alg. iterative-minorant): mu := 0, then max_pass
+ *   passes over the chain, forward first and then alternating; at each node the
+ *   min-marginal m_i of the remainder f - mu is drained by mu_i +=
+ *   floor(gamma m_i), gamma = gamma_num / gamma_den on every pass but the last,
+ *   where gamma = 1 (the minorant is then maximal).
+ * Both alternatives run on the int32 kernel (one warp per chain) and give the
+ * same numbers as the oracle.  Changing the minorant of a context that holds a
+ * cost volume chooses the dual storage again and resets the duals.
+ * DM_ERR_ARG for an unknown kind or, for the iterative minorant, max_pass
+ * outside [1, 64], gamma_den outside [1, 1024] or gamma_num outside
+ * [0, gamma_den]; the other arguments are ignored for the first two kinds.
+ * The batched form uses the hierarchical minorant only (a batch whose context
+ * was switched reports DM_ERR_STATE). */
+#define DM_MINORANT_HIER      0
+#define DM_MINORANT_NAIVE     1
+#define DM_MINORANT_ITERATIVE 2
+DM_API int dm_set_minorant(dm_ctx* ctx, int kind, int max_pass, int gamma_num, int gamma_den);
+
 /* The Dual MM kernel chosen for the current cost volume: *kernel = 16 (packed
  * 16-bit arithmetic, dual deltas of *delta_bytes bytes per label) or 32 (int32
  * kernel, *delta_bytes = 4).  Host only. */

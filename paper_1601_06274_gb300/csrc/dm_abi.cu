@@ -316,8 +316,9 @@ int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
 void set_path(dm_ctx* c, int cost_max, bool user_weights)
 {
     const int p2 = user_weights ? c->p2_all : c->p2_used;
+    c->user_weights = user_weights;
     c->cost_max = cost_max;
-    c->use16 = c->can16 && cost_max + 2 * (p2 + 1) <= kMaxDelta16;
+    c->use16 = c->can16 && c->minorant == 0 && cost_max + 2 * (p2 + 1) <= kMaxDelta16;
     c->delta_bytes = (cost_max + 2 * (p2 + 1) <= 255) ? 1 : 2;
 }
 
@@ -358,6 +359,10 @@ int run_pass(dm_ctx* c, int which, uint16_t* labels, long long* lb)
     a.err = reinterpret_cast<int32_t*>(ws + c->lay.err);
     a.labels = labels;
     a.lb = lb;
+    a.minorant = c->minorant;
+    a.max_pass = c->max_pass;
+    a.gamma_num = c->gamma_num;
+    a.gamma_den = c->gamma_den;
     DM_CK(dm::launch_dmm_pass(a, c->lpt, c->radius, c->stream));
     c->launches += 1;
     return DM_OK;
@@ -1289,6 +1294,25 @@ DM_API int dm_solve_host(dm_ctx* ctx, const uint8_t* h_left, const uint8_t* h_ri
         DM_CK(cudaMemcpyAsync(h_labels, ctx->ws + ctx->lay.labels, HW * sizeof(uint16_t),
                               cudaMemcpyDeviceToHost, ctx->stream));
     return check_device_error(ctx);
+}
+
+DM_API int dm_set_minorant(dm_ctx* ctx, int kind, int max_pass, int gamma_num, int gamma_den)
+{
+    if (ctx == nullptr || kind < DM_MINORANT_HIER || kind > DM_MINORANT_ITERATIVE) return DM_ERR_ARG;
+    if (kind == DM_MINORANT_ITERATIVE &&
+        (max_pass < 1 || max_pass > 64 || gamma_den < 1 || gamma_den > 1024 || gamma_num < 0 ||
+         gamma_num > gamma_den))
+        return DM_ERR_ARG;
+    ctx->minorant = kind;
+    if (kind == DM_MINORANT_ITERATIVE) {
+        ctx->max_pass = max_pass;
+        ctx->gamma_num = gamma_num;
+        ctx->gamma_den = gamma_den;
+    }
+    if (ctx->ws == nullptr || !ctx->have_cost) return DM_OK;
+    // the dual storage follows the kernel: choose it again and start cold
+    set_path(ctx, ctx->cost_max, ctx->user_weights);
+    return dm_reset_duals(ctx);
 }
 
 DM_API int dm_get_path(const dm_ctx* ctx, int* kernel, int* delta_bytes)

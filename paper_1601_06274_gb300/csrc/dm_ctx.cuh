@@ -46,6 +46,10 @@ struct dm_ctx {
     // two-view solve: fork to the right view's stream and join back (created on
     // first use, destroyed by dm_destroy)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // chain minorant of the Dual MM passes (0 hierarchical; 1 naive and 2
+    // iterative run on the int32 kernel)
+    int minorant = 0, max_pass = 3, gamma_num = 1, gamma_den = 4;
+    bool user_weights = false;  // the current edge weights came from the caller
 };
 
 namespace dm {

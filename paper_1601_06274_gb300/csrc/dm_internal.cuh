@@ -48,6 +48,9 @@ struct DmmArgs {
     // finalisation (last vertical pass of a dm_discrete call)
     uint16_t* labels;       // nullable: per-pixel argmin of lambda_h + lambda_v
     long long* lb;          // nullable: sum_i min_l (lambda_h + lambda_v)_i(l)
+    // chain minorant: 0 hierarchical (App. A), 1 naive, 2 iterative with
+    // max_pass passes and gamma = gamma_num / gamma_den before the last pass
+    int minorant, max_pass, gamma_num, gamma_den;
 };
 
 // Packed 16-bit Dual MM pass (dmm16.cu).  Duals are stored as an int32 base per

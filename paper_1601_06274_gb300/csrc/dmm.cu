@@ -313,11 +313,231 @@ __global__ void __launch_bounds__(kWarps * 32) dmm_pass_kernel(const DmmArgs A)
         atomicAdd(reinterpret_cast<unsigned long long*>(A.lb), (unsigned long long)lb_acc);
 }
 
+// ---------------------------------------------------------------------------
+// Other chain minorants (Sec. 2.3 "Good and Fast Minorants"; App. A).
+//   naive (KIND 1): every node takes floor(m_i / n) of its min-marginal m_i.
+//   iterative (KIND 2, Alg. iterative-minorant): mu := 0, then max_pass passes
+//     alternating in direction (forward first); at node i the min-marginal of
+//     the remainder f - mu is F_i + theta_i - mu_i + B_i, where the message from
+//     the side visited earlier in the pass is formed as the pass goes and the
+//     other one was stored by the previous pass (an initial backward sweep
+//     before the first), and mu_i += floor(gamma m_i), gamma = 1 on the last
+//     pass.
+// One warp per chain, labels across its lanes as in dmm_pass_kernel; a sweep
+// stores the messages it forms (F or B) for the next pass, which runs the
+// other way.  mu accumulates in lam_out; each node's final visit writes
+// lam_out = mu - lam_in and takes the labels and the bound.  The next node's
+// unaries, stored message and mu are loaded one step ahead.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int floor_div64(long long a, int d)
+{
+    return (int)(a >= 0 ? a / d : -((-a + d - 1) / d));
+}
+
+__device__ __forceinline__ int floor_div32(int a, int d)
+{
+    return a >= 0 ? a / d : -((-a + d - 1) / d);
+}
+
+// floor(m * num / den) for the pass's gamma = num / den (0 <= num <= den): m
+// itself for gamma = 1, an arithmetic shift (a floor) for 1 / 2^s, 32-bit
+// division for 1 / den, 64-bit otherwise; the case is the same for the warp
+__device__ __forceinline__ int gamma_part(int m, int num, int den, int shift)
+{
+    if (num == den) return m;
+    if (num == 1) return shift >= 0 ? (m >> shift) : floor_div32(m, den);
+    return floor_div64((long long)m * num, den);
+}
+
+template <int LPT>
+struct NodeIn {
+    int th[LPT], other[LPT], mu[LPT];
+    int om;  // weight of the edge the sweep leaves node k by (-1: none)
+};
+
+// penalty taps of weight om (flags a weight without an integer table)
+__device__ __forceinline__ const int* taps_for(const DmmArgs& A, int om)
+{
+    const int* tap = A.taps + om * kTapW;
+    if (__ldg(tap + kTapValid) == 0) atomicOr(A.err, kDevErrBadOmega);
+    return tap;
+}
+
+template <int LPT>
+__device__ __forceinline__ void load_node(const DmmArgs& A, const Chain& ch, const int32_t* obuf,
+                                          int k, int edge, bool load_mu, int lane, NodeIn<LPT>& nd)
+{
+    nd.om = edge >= 0 ? (int)__ldg(A.wedge + ch.pix(edge)) : -1;
+    load_theta<LPT>(A, ch, k, lane, nd.th);
+    if (obuf != nullptr) load_msg<LPT>(obuf + (size_t)k * A.KP, lane, nd.other);
+    const size_t base = ch.pix(k) * (size_t)ch.L + (size_t)lane * LPT;
+#pragma unroll
+    for (int j = 0; j < LPT; ++j)
+        nd.mu[j] = (load_mu && lane * LPT + j < ch.L) ? A.lam_out[base + j] : 0;
+}
+
+// bring node k's inputs towards L2 ahead of the one-step register prefetch
+// (a chain has one warp, so the latency of DRAM is not hidden by other warps)
+constexpr int kL2Ahead = 8;
+
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+template <int LPT>
+__device__ __forceinline__ void prefetch_node(const DmmArgs& A, const Chain& ch, const int32_t* obuf,
+                                              int k, bool mu, int lane)
+{
+    const size_t base = ch.pix(k) * (size_t)ch.L + (size_t)lane * LPT;
+    if (lane * LPT < ch.L) {
+        prefetch_l2(A.lam_in + base);
+        if (ch.which == 0)
+            prefetch_l2(A.cost16 != nullptr ? (const void*)(A.cost16 + base)
+                                            : (const void*)(A.cost + base));
+        if (mu) prefetch_l2(A.lam_out + base);
+    }
+    if (obuf != nullptr) prefetch_l2(obuf + (size_t)k * A.KP + (size_t)lane * LPT);
+}
+
+template <int LPT>
+__device__ __forceinline__ void finalise_node(const DmmArgs& A, const Chain& ch, int k, int lane,
+                                              const int (&mu)[LPT], long long& lb_acc)
+{
+    const size_t pix = ch.pix(k);
+    const size_t base = pix * (size_t)A.L + (size_t)lane * LPT;
+    int best = kInf, arg = 0x7fffffff;
+#pragma unroll
+    for (int j = 0; j < LPT; ++j) {
+        const int l = lane * LPT + j;
+        if (l < A.L) {
+            A.lam_out[base + j] = mu[j] - __ldg(A.lam_in + base + j);
+            if (mu[j] < best) {            // lambda_h + lambda_v = mu
+                best = mu[j];
+                arg = l;
+            }
+        }
+    }
+    if (A.labels != nullptr || A.lb != nullptr) {
+        const int m = __reduce_min_sync(kFull, best);
+        if (A.labels != nullptr) {
+            const int cand = (best == m) ? arg : 0x7fffffff;
+            const int am = __reduce_min_sync(kFull, cand);
+            if (lane == 0) A.labels[pix] = (uint16_t)am;
+        }
+        lb_acc += m;
+    }
+}
+
+template <int LPT, int R, bool PAD, int KIND>
+__global__ void __launch_bounds__(32) dmm_alt_kernel(const DmmArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    Chain ch;
+    ch.which = A.which;
+    ch.W = A.W;
+    ch.L = A.L;
+    ch.KP = A.KP;
+    ch.n = A.which == 0 ? A.W : A.H;
+    ch.c = blockIdx.x;
+    const int n = ch.n;
+    int32_t* F = A.fmsg + (size_t)ch.c * n * A.KP;
+    int32_t* B = A.bmsg + (size_t)ch.c * n * A.KP;
+    const int passes = KIND == 1 ? 1 : A.max_pass;
+    int msgv[LPT], x[LPT];
+    long long lb_acc = 0;
+
+    // backward sweep of the chain with mu = 0: B_{k-1} = Msg(theta_k + B_k)
+#pragma unroll
+    for (int j = 0; j < LPT; ++j) msgv[j] = 0;
+    store_msg<LPT>(B + (size_t)(n - 1) * A.KP, lane, msgv);
+    {
+        NodeIn<LPT> cur, nxt;
+        if (n > 1) load_node<LPT>(A, ch, nullptr, n - 1, n - 2, false, lane, cur);
+        for (int k = n - 1; k > 0; --k) {
+            if (k - kL2Ahead >= 0) prefetch_node<LPT>(A, ch, nullptr, k - kL2Ahead, false, lane);
+            if (k > 1) load_node<LPT>(A, ch, nullptr, k - 1, k - 2, false, lane, nxt);
+            const int* tap = taps_for(A, cur.om);
+#pragma unroll
+            for (int j = 0; j < LPT; ++j) x[j] = cur.th[j] + msgv[j];
+            msg<LPT, R, PAD>(x, msgv, tap, lane, A.L);
+            store_msg<LPT>(B + (size_t)(k - 1) * A.KP, lane, msgv);
+            cur = nxt;
+        }
+    }
+
+    for (int s = 1; s <= passes; ++s) {
+        const bool last = s == passes;
+        const bool fwd = (s & 1) == 1;
+        const int num = KIND == 1 ? 1 : (last ? 1 : A.gamma_num);
+        const int den = KIND == 1 ? n : (last ? 1 : A.gamma_den);
+        const int shift = (den & (den - 1)) == 0 ? __ffs(den) - 1 : -1;  // den = 2^shift
+        int32_t* obuf = fwd ? B : F;     // messages from the side not yet visited
+        int32_t* sbuf = fwd ? F : B;     // messages this pass forms, kept for the next
+#pragma unroll
+        for (int j = 0; j < LPT; ++j) msgv[j] = 0;
+        NodeIn<LPT> cur, nxt;
+        // node k's outgoing edge: k (forward) or k - 1 (backward), none at the far end
+        auto edge_of = [&](int k) { return fwd ? (k + 1 < n ? k : -1) : k - 1; };
+        load_node<LPT>(A, ch, obuf, fwd ? 0 : n - 1, edge_of(fwd ? 0 : n - 1), s > 1, lane, cur);
+        for (int t = 0; t < n; ++t) {
+            const int k = fwd ? t : n - 1 - t;
+            if (t + kL2Ahead < n)
+                prefetch_node<LPT>(A, ch, obuf, fwd ? k + kL2Ahead : k - kL2Ahead, s > 1, lane);
+            if (t + 1 < n)
+                load_node<LPT>(A, ch, obuf, fwd ? k + 1 : k - 1, edge_of(fwd ? k + 1 : k - 1),
+                               s > 1, lane, nxt);
+            const int* tap = cur.om >= 0 ? taps_for(A, cur.om) : nullptr;
+            if (!last) store_msg<LPT>(sbuf + (size_t)k * A.KP, lane, msgv);
+#pragma unroll
+            for (int j = 0; j < LPT; ++j) {
+                if (lane * LPT + j < A.L) {
+                    const int m = msgv[j] + cur.th[j] - cur.mu[j] + cur.other[j];
+                    cur.mu[j] += gamma_part(m, num, den, shift);
+                }
+            }
+            if (last) {
+                finalise_node<LPT>(A, ch, k, lane, cur.mu, lb_acc);
+            } else {
+                const size_t base = ch.pix(k) * (size_t)ch.L + (size_t)lane * LPT;
+#pragma unroll
+                for (int j = 0; j < LPT; ++j)
+                    if (lane * LPT + j < A.L) A.lam_out[base + j] = cur.mu[j];
+            }
+            if (t + 1 < n) {
+                // the naive minorant takes the min-marginals of f itself; the
+                // iterative one those of the remainder f - mu, mu_k just updated
+#pragma unroll
+                for (int j = 0; j < LPT; ++j)
+                    x[j] = cur.th[j] - (KIND == 1 ? 0 : cur.mu[j]) + msgv[j];
+                msg<LPT, R, PAD>(x, msgv, tap, lane, A.L);
+                cur = nxt;
+            }
+        }
+    }
+    if (A.lb != nullptr && lane == 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(A.lb), (unsigned long long)lb_acc);
+}
+
+template <int LPT, int R, int KIND>
+void launch_alt(const DmmArgs& a, int chains, cudaStream_t s)
+{
+    if (a.L == 32 * LPT)
+        dmm_alt_kernel<LPT, R, false, KIND><<<chains, 32, 0, s>>>(a);
+    else
+        dmm_alt_kernel<LPT, R, true, KIND><<<chains, 32, 0, s>>>(a);
+}
+
 template <int LPT, int R>
 cudaError_t launch_lr(const DmmArgs& a, cudaStream_t s)
 {
     const int chains = a.which == 0 ? a.H : a.W;
-    if (a.L == 32 * LPT)
+    if (a.minorant == 1)
+        launch_alt<LPT, R, 1>(a, chains, s);
+    else if (a.minorant == 2)
+        launch_alt<LPT, R, 2>(a, chains, s);
+    else if (a.L == 32 * LPT)
         dmm_pass_kernel<LPT, R, false><<<chains, kWarps * 32, 0, s>>>(a);
     else
         dmm_pass_kernel<LPT, R, true><<<chains, kWarps * 32, 0, s>>>(a);

@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
             "dm_cost_volume_warm": [_vp, _vp, _vp],
             "dm_solve_next": [_vp, _vp, _vp, _i, _i, _vp],
             "dm_cost_volume_mirrored": [_vp, _vp, _vp],
+            "dm_set_minorant": [_vp, _i, _i, _i, _i],
             "dm_lr_check": [_vp, _vp, _i, _i, ctypes.c_float, _vp, _vp, _vp, _vp],
             "dm_solve_lr": [_vp, _vp, _vp, _vp, _i, _i, ctypes.c_float, _vp, _vp, _vp],
             "dm_set_data_weights": [_vp, _vp],
@@ -140,6 +141,9 @@ def _ptr(t) -> int | None:
     if t is None:
         return None
     return t.data_ptr()
+
+
+MINORANTS = {"hier": 0, "naive": 1, "iterative": 2}
 
 
 class Context:
@@ -222,6 +226,12 @@ class Context:
         _ck(lib().dm_set_cost_volume_u16(self._h, self._c.data_ptr(), self._wh.data_ptr(),
                                          self._wv.data_ptr(), int(cost_max)),
             "dm_set_cost_volume_u16")
+
+    def set_minorant(self, kind: str = "hier", max_pass: int = 3, gamma=(1, 4)):
+        """Chain minorant of the Dual MM passes: "hier" (default), "naive" or
+        "iterative" (max_pass passes, gamma = gamma[0] / gamma[1] but the last)."""
+        _ck(lib().dm_set_minorant(self._h, MINORANTS[kind], int(max_pass), int(gamma[0]),
+                                  int(gamma[1])), "dm_set_minorant")
 
     def cost_volume_mirrored(self, left, right):
         """The right view's problem of (left, right), in mirrored columns."""

@@ -203,3 +203,18 @@ def test_two_view_calls_check_arguments_without_gpu(lib):
         assert lib.dm_lr_check(ul, um, H, W, md, ok, out, None, None) == dm.DM_ERR_ARG
     lib.dm_destroy(a)
     lib.dm_destroy(b)
+
+
+def test_set_minorant_checks_arguments_without_gpu(lib):
+    from paper_1601_06274_gb300 import dm
+    p = dm.default_params()
+    h = ctypes.c_void_p()
+    assert lib.dm_create(8, 8, 16, ctypes.byref(p), ctypes.byref(h)) == 0
+    assert lib.dm_set_minorant(h, 1, 0, 0, 0) == dm.DM_OK       # naive ignores the rest
+    assert lib.dm_set_minorant(h, 2, 3, 1, 4) == dm.DM_OK
+    assert lib.dm_set_minorant(h, 0, 0, 0, 0) == dm.DM_OK
+    for args in [(3, 3, 1, 4), (-1, 3, 1, 4), (2, 0, 1, 4), (2, 65, 1, 4), (2, 3, 5, 4),
+                 (2, 3, -1, 4), (2, 3, 1, 0), (2, 3, 1, 2000)]:
+        assert lib.dm_set_minorant(h, *args) == dm.DM_ERR_ARG, args
+    assert lib.dm_set_minorant(None, 0, 0, 0, 0) == dm.DM_ERR_ARG
+    lib.dm_destroy(h)
