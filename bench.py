@@ -382,7 +382,11 @@ KERNEL_NAMES = {16: "dmm16_kernel", 32: "dmm_pass_kernel"}
 # profiles/ of the kernel as built now (keyed by workload and kernel); a kernel
 # changed since its capture has no entry and reports null
 NCU_TRAFFIC = {("kitti", "dmm16_kernel horizontal pass"): 351_220_224,
-               ("kitti", "dmm16_kernel vertical pass"): 289_238_272}
+               ("kitti", "dmm16_kernel vertical pass"): 289_238_272,
+               # dram__bytes.sum.per_second x gpu__time_duration.sum of the capture
+               ("minorants", "dmm_alt_kernel horizontal pass"): 3_585_900_000,
+               ("minorants", "dmm_alt_kernel vertical pass"): 3_333_000_000,
+               ("lr", "lr_check_kernel"): 3_732_000}
 # smsp__inst_executed.sum per launch from the same capture: the pass is bound by
 # instruction issue, so its issue rate is reported beside the HBM roofline,
 # against 152 SMs x 4 schedulers x 1 warp-instruction per cycle at 2070 MHz
@@ -731,6 +735,7 @@ def run_lr(args):
     roofline["check_kernel"] = {"kernel": "lr_check_kernel", "us": round(chk_ms * 1e3, 2),
                                 "timing": f"{NB} launches on rotating buffers in one graph",
                                 "bytes_per_launch": LR_CHECK_BYTES * H * W,
+                                "traffic": NCU_TRAFFIC.get(("lr", "lr_check_kernel")),
                                 "achieved_gbs": round(chk_gbs, 1),
                                 "frac": round(chk_gbs / peak, 4)}
 
@@ -853,6 +858,7 @@ def run_minorants(args):
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "kernel": "dmm_alt_kernel " + ("horizontal" if dom == 0 else "vertical") + " pass",
                 "peak_source": src, "bytes_per_launch": bytes_per[dom]}
+    roofline["traffic"] = NCU_TRAFFIC.get(("minorants", roofline["kernel"]))
 
     cpu = None
     if not args.no_cpu_baseline:
