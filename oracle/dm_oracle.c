@@ -707,6 +707,238 @@ int or_refine(int H, int W, int L, const double* cost, const double* alpha, cons
     return OR_OK;
 }
 
+/* ======================================================================== */
+/* Optical flow (Sec. 2.2 "Flow"; the appendix section on optical flow).    */
+/* The displacement of pixel (y, x) is (d1, d2), d1 horizontal, d2 vertical, */
+/* with d_k = lo_k + label (labels 0..K_k-1; reading R31).                   */
+/* ======================================================================== */
+
+typedef struct {
+    int H, W, lo1, K1, lo2, K2, maxc;
+    const uint32_t* c1;   /* census of I1 */
+    const uint32_t* c2;   /* census of I2 */
+} or_flow_geo;
+
+/* discretised data cost D_i(d1, d2) = Hamming(census1(y, x), census2(y + d2, x + d1)),
+ * maxc where the displaced pixel leaves the image (reading R31) */
+static i64 flow_cost_at(const or_flow_geo* G, int y, int x, int d1, int d2)
+{
+    int yy = y + d2, xx = x + d1;
+    if (yy < 0 || yy >= G->H || xx < 0 || xx >= G->W) return G->maxc;
+    return popcount32(G->c1[(i64)y * G->W + x] ^ G->c2[(i64)yy * G->W + xx]);
+}
+
+/* Decoupled costs (Eq. flow decoupled costs): p1[y][x][l1] = min_l2 D(l1, l2),
+ * p2[y][x][l2] = min_l1 D(l1, l2). */
+int or_flow_cost_projected(const or_flow_geo* G, int32_t* p1, int32_t* p2)
+{
+    if (G->H <= 0 || G->W <= 0 || G->K1 <= 0 || G->K2 <= 0) return OR_ERR_ARG;
+    for (int y = 0; y < G->H; ++y)
+        for (int x = 0; x < G->W; ++x) {
+            i64 px = (i64)y * G->W + x;
+            for (int a = 0; a < G->K1; ++a) p1[px * G->K1 + a] = INT32_MAX;
+            for (int b = 0; b < G->K2; ++b) p2[px * G->K2 + b] = INT32_MAX;
+            for (int a = 0; a < G->K1; ++a)
+                for (int b = 0; b < G->K2; ++b) {
+                    int32_t v = (int32_t)flow_cost_at(G, y, x, G->lo1 + a, G->lo2 + b);
+                    if (v < p1[px * G->K1 + a]) p1[px * G->K1 + a] = v;
+                    if (v < p2[px * G->K2 + b]) p2[px * G->K2 + b] = v;
+                }
+        }
+    return OR_OK;
+}
+
+/* Continuous data term at label coordinates (v1, v2): bilinear interpolation of
+ * the integer costs, each argument clamped to [0, K_k - 1] (reading R33). */
+double or_flow_D(const or_flow_geo* G, int y, int x, double v1, double v2)
+{
+    if (v1 < 0.0) v1 = 0.0;
+    if (v1 > G->K1 - 1) v1 = G->K1 - 1;
+    if (v2 < 0.0) v2 = 0.0;
+    if (v2 > G->K2 - 1) v2 = G->K2 - 1;
+    int a = (int)floor(v1), b = (int)floor(v2);
+    if (a > G->K1 - 2) a = G->K1 - 2 < 0 ? 0 : G->K1 - 2;
+    if (b > G->K2 - 2) b = G->K2 - 2 < 0 ? 0 : G->K2 - 2;
+    double t = v1 - a, s = v2 - b;
+    int a1 = a + 1 < G->K1 ? a + 1 : a, b1 = b + 1 < G->K2 ? b + 1 : b;
+    double d00 = (double)flow_cost_at(G, y, x, G->lo1 + a, G->lo2 + b);
+    double d10 = (double)flow_cost_at(G, y, x, G->lo1 + a1, G->lo2 + b);
+    double d01 = (double)flow_cost_at(G, y, x, G->lo1 + a, G->lo2 + b1);
+    double d11 = (double)flow_cost_at(G, y, x, G->lo1 + a1, G->lo2 + b1);
+    return (1 - t) * (1 - s) * d00 + t * (1 - s) * d10 + (1 - t) * s * d01 + t * s * d11;
+}
+
+/* Quadratic fit (Eq. quadfit) from the 3x3 samples S[j][i] = D(u0 + (i-1) h e1 +
+ * (j-1) h e2): L = central first differences, Q = second differences (the mixed
+ * term from the four corners), all with step h (reading R35). */
+void or_flow_fit_samples(const double* S, double h, double* L, double* Q)
+{
+    L[0] = (S[1 * 3 + 2] - S[1 * 3 + 0]) / (2.0 * h);
+    L[1] = (S[2 * 3 + 1] - S[0 * 3 + 1]) / (2.0 * h);
+    Q[0] = (S[1 * 3 + 2] - 2.0 * S[1 * 3 + 1] + S[1 * 3 + 0]) / (h * h);        /* q11 */
+    Q[1] = (S[2 * 3 + 2] - S[0 * 3 + 2] - S[2 * 3 + 0] + S[0 * 3 + 0]) / (4.0 * h * h); /* q12 */
+    Q[2] = (S[2 * 3 + 1] - 2.0 * S[1 * 3 + 1] + S[0 * 3 + 1]) / (h * h);        /* q22 */
+}
+
+/* Positive-semidefinite part of the symmetric 2x2 [[q11, q12], [q12, q22]]: the
+ * eigenvalues below zero are set to zero (Werlberger et al.; reading R35). */
+void or_psd2(double* Q)
+{
+    double a = Q[0], b = Q[1], c = Q[2];
+    double m = 0.5 * (a + c), r = sqrt(0.25 * (a - c) * (a - c) + b * b);
+    double lp = m + r, lm = m - r;
+    if (lm >= 0.0) return;
+    if (lp <= 0.0) { Q[0] = Q[1] = Q[2] = 0.0; return; }
+    /* keep lp v v^T, v the unit eigenvector of lp */
+    double v1, v2;
+    if (fabs(b) > 0.0) {
+        v1 = b; v2 = lp - a;
+        if (fabs(v1) + fabs(v2) == 0.0) { v1 = lp - c; v2 = b; }
+    } else if (a >= c) { v1 = 1.0; v2 = 0.0; }
+    else { v1 = 0.0; v2 = 1.0; }
+    double n = sqrt(v1 * v1 + v2 * v2);
+    v1 /= n; v2 /= n;
+    Q[0] = lp * v1 * v1;
+    Q[1] = lp * v1 * v2;
+    Q[2] = lp * v2 * v2;
+}
+
+/* L, Q (PSD part) of alpha D at u0 and the box, for one pixel */
+void or_flow_linearise_px(const or_flow_geo* G, int y, int x, double alpha, double u01,
+                          double u02, double h, double* L, double* Q, double* box)
+{
+    double S[9];
+    for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i)
+            S[j * 3 + i] = alpha * or_flow_D(G, y, x, u01 + (i - 1) * h, u02 + (j - 1) * h);
+    or_flow_fit_samples(S, h, L, Q);
+    or_psd2(Q);
+    box[0] = u01 - h > 0.0 ? u01 - h : 0.0;
+    box[1] = u01 + h < G->K1 - 1 ? u01 + h : G->K1 - 1;
+    box[2] = u02 - h > 0.0 ? u02 - h : 0.0;
+    box[3] = u02 + h < G->K2 - 1 ? u02 + h : G->K2 - 1;
+}
+
+/* prox of tau D~ for the quadratic model (Eq. prox_flow re-derived, reading R36):
+ * u = (I + tau Q)^{-1} (uh + tau (Q u0 - L)), then each component clamped to its box */
+void or_flow_prox(double uh1, double uh2, double u01, double u02, const double* L,
+                  const double* Q, const double* box, double tau, double* u1, double* u2)
+{
+    double r1 = uh1 + tau * (Q[0] * u01 + Q[1] * u02 - L[0]);
+    double r2 = uh2 + tau * (Q[1] * u01 + Q[2] * u02 - L[1]);
+    double m11 = 1.0 + tau * Q[0], m12 = tau * Q[1], m22 = 1.0 + tau * Q[2];
+    double det = m11 * m22 - m12 * m12;
+    double v1 = (m22 * r1 - m12 * r2) / det;
+    double v2 = (m11 * r2 - m12 * r1) / det;
+    if (v1 < box[0]) v1 = box[0];
+    if (v1 > box[1]) v1 = box[1];
+    if (v2 < box[2]) v2 = box[2];
+    if (v2 > box[3]) v2 = box[3];
+    *u1 = v1;
+    *u2 = v2;
+}
+
+/* E(u) = sum_i alpha D_i(u_i) + sum_k sum_e lambda_r omega_e r((A u^k)_e) (reading R34) */
+double or_flow_energy(const or_flow_geo* G, double alpha, const double* wh, const double* wv,
+                      const or_cont_params* P, const double* u1, const double* u2)
+{
+    double e = 0.0;
+    int H = G->H, W = G->W;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            i64 p = (i64)y * W + x;
+            e += alpha * or_flow_D(G, y, x, u1[p], u2[p]);
+            for (int k = 0; k < 2; ++k) {
+                const double* u = k == 0 ? u1 : u2;
+                if (x + 1 < W) e += P->lambda_r * wh[p] * or_r(u[p] - u[p + 1], P->eps, P->delta, P->C);
+                if (y + 1 < H) e += P->lambda_r * wv[p] * or_r(u[p] - u[p + W], P->eps, P->delta, P->C);
+            }
+        }
+    return e;
+}
+
+/* Primal-dual refinement of the flow (Sec. 2.4 iterates, the appendix's
+ * quadratic data model): as or_refine, with two components that share the
+ * primal prox and have a regulariser each (reading R34, R37).  u1, u2 hold
+ * the start (label coordinates) on entry; D (8 arrays: ph1 pv1 qh1 qv1 ph2 pv2
+ * qh2 qv2, H*W each) holds the duals; init resets them to 0. */
+int or_flow_refine(const or_flow_geo* G, double alpha, const double* wh, const double* wv,
+                   int iters, const or_cont_params* P, double* u1, double* u2, double* D, int init,
+                   double* energy)
+{
+    int H = G->H, W = G->W;
+    if (H <= 0 || W <= 0 || G->K1 < 2 || G->K2 < 2 || P->warps <= 0) return OR_ERR_ARG;
+    i64 N = (i64)H * W;
+    double* Lf = (double*)malloc(2 * N * sizeof(double));
+    double* Qf = (double*)malloc(3 * N * sizeof(double));
+    double* Bx = (double*)malloc(4 * N * sizeof(double));
+    double* U0 = (double*)malloc(2 * N * sizeof(double));
+    double* un1 = (double*)malloc(N * sizeof(double));
+    double* un2 = (double*)malloc(N * sizeof(double));
+    if (init) for (i64 e = 0; e < 8 * N; ++e) D[e] = 0.0;
+    double* ph[2] = {D, D + 4 * N};
+    double* pv[2] = {D + N, D + 5 * N};
+    double* qh[2] = {D + 2 * N, D + 6 * N};
+    double* qv[2] = {D + 3 * N, D + 7 * N};
+    double* u[2] = {u1, u2};
+    double* un[2] = {un1, un2};
+    const double bp = P->delta, ap = P->eps, bq = P->C + P->delta - P->eps * P->delta;
+    const double tau = P->tau, sigma = P->sigma;
+    int base = iters / P->warps, extra = iters % P->warps;
+    for (int w = 0; w < P->warps; ++w) {
+        int nit = base + (w < extra ? 1 : 0);
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                i64 p = (i64)y * W + x;
+                U0[2 * p] = u1[p];
+                U0[2 * p + 1] = u2[p];
+                or_flow_linearise_px(G, y, x, alpha, u1[p], u2[p], P->h, Lf + 2 * p, Qf + 3 * p,
+                                     Bx + 4 * p);
+            }
+        for (int it = 0; it < nit; ++it) {
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    i64 p = (i64)y * W + x;
+                    double uh[2];
+                    for (int k = 0; k < 2; ++k) {
+                        double div = 0.0;
+                        if (x + 1 < W) div += ph[k][p] - qh[k][p];
+                        if (x > 0) div -= ph[k][p - 1] - qh[k][p - 1];
+                        if (y + 1 < H) div += pv[k][p] - qv[k][p];
+                        if (y > 0) div -= pv[k][p - W] - qv[k][p - W];
+                        uh[k] = u[k][p] - tau * div;
+                    }
+                    or_flow_prox(uh[0], uh[1], U0[2 * p], U0[2 * p + 1], Lf + 2 * p, Qf + 3 * p,
+                                 Bx + 4 * p, tau, &un1[p], &un2[p]);
+                }
+            for (int k = 0; k < 2; ++k)
+                for (int y = 0; y < H; ++y)
+                    for (int x = 0; x < W; ++x) {
+                        i64 p = (i64)y * W + x;
+                        if (x + 1 < W) {
+                            double om = P->lambda_r * wh[p];
+                            double au = u[k][p] - u[k][p + 1];
+                            double ext = (2.0 * un[k][p] - u[k][p]) - (2.0 * un[k][p + 1] - u[k][p + 1]);
+                            qh[k][p] = or_prox_conj(qh[k][p] + tau * au, om, 0.0, bq, tau);
+                            ph[k][p] = or_prox_conj(ph[k][p] + sigma * ext, om, ap, bp, sigma);
+                        }
+                        if (y + 1 < H) {
+                            double om = P->lambda_r * wv[p];
+                            double au = u[k][p] - u[k][p + W];
+                            double ext = (2.0 * un[k][p] - u[k][p]) - (2.0 * un[k][p + W] - u[k][p + W]);
+                            qv[k][p] = or_prox_conj(qv[k][p] + tau * au, om, 0.0, bq, tau);
+                            pv[k][p] = or_prox_conj(pv[k][p] + sigma * ext, om, ap, bp, sigma);
+                        }
+                    }
+            memcpy(u1, un1, N * sizeof(double));
+            memcpy(u2, un2, N * sizeof(double));
+        }
+        if (energy) energy[w] = or_flow_energy(G, alpha, wh, wv, P, u1, u2);
+    }
+    free(Lf); free(Qf); free(Bx); free(U0); free(un1); free(un2);
+    return OR_OK;
+}
+
 /* Primal and dual objective of the convex problem obtained when R- vanishes
  * (C -> infinity) for a fixed linearisation (used to check that the
  * primal-dual gap closes).  primal = sum D~_i(u_i) + sum lambda_r omega r_{eps,delta}(Au);

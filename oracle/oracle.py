@@ -36,6 +36,12 @@ class ContParams(ctypes.Structure):
                 ("sigma", ctypes.c_double), ("h", ctypes.c_double), ("warps", ctypes.c_int)]
 
 
+class FlowGeo(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("lo1", ctypes.c_int),
+                ("K1", ctypes.c_int), ("lo2", ctypes.c_int), ("K2", ctypes.c_int),
+                ("maxc", ctypes.c_int), ("c1", u32p), ("c2", u32p)]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle (gcc -O2, OpenMP) into oracle/_build/."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -56,6 +62,22 @@ def lib():
         L = _lib
         L.or_census.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int, u32p]
         L.or_cost_volume.argtypes = [ctypes.c_int] * 3 + [u32p, u32p, ctypes.c_int, i32p]
+        G = ctypes.POINTER(FlowGeo)
+        L.or_flow_cost_projected.argtypes = [G, i32p, i32p]
+        L.or_flow_D.argtypes = [G, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.or_flow_D.restype = ctypes.c_double
+        L.or_flow_fit_samples.argtypes = [f64p, ctypes.c_double, f64p, f64p]
+        L.or_psd2.argtypes = [f64p]
+        L.or_flow_linearise_px.argtypes = [G, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 \
+            + [f64p, f64p, f64p]
+        L.or_flow_prox.argtypes = [ctypes.c_double] * 4 + [f64p, f64p, f64p, ctypes.c_double,
+                                                           f64p, f64p]
+        L.or_flow_energy.argtypes = [G, ctypes.c_double, f64p, f64p, ctypes.POINTER(ContParams),
+                                     f64p, f64p]
+        L.or_flow_energy.restype = ctypes.c_double
+        L.or_flow_refine.argtypes = [G, ctypes.c_double, f64p, f64p, ctypes.c_int,
+                                     ctypes.POINTER(ContParams), f64p, f64p, f64p, ctypes.c_int,
+                                     f64p]
         L.or_cost_volume_right.argtypes = [ctypes.c_int] * 3 + [u32p, u32p, ctypes.c_int, i32p]
         L.or_lr_check.argtypes = [ctypes.c_int, ctypes.c_int, f32p, f32p, ctypes.c_float, u8p,
                                   f32p]
@@ -448,3 +470,104 @@ def solve_lr(left, right, L: int, dmm_iters: int, pd_iters: int, P: Params = Par
     u_right = np.ascontiguousarray(sm["u"][:, ::-1]).astype(np.float32)
     ok, out = lr_check(u_left, u_right, max_diff)
     return dict(left=sl, mirrored=sm, u_left=u_left, u_right=u_right, ok=ok, u=out)
+
+
+# ---------------------------------------------------------------------------
+# Optical flow (Sec. 2.2 "Flow"; the appendix's quadratic data model)
+# ---------------------------------------------------------------------------
+
+class Flow:
+    """Flow geometry: images I1, I2 (uint8 [H, W]), displacement d_k = lo_k + label,
+    labels 0..K_k-1 (d1 horizontal, d2 vertical)."""
+
+    def __init__(self, img1, img2, lo1: int, K1: int, lo2: int, K2: int, win: int = 5):
+        self.img1 = np.ascontiguousarray(img1, dtype=np.uint8)
+        self.img2 = np.ascontiguousarray(img2, dtype=np.uint8)
+        self.H, self.W = self.img1.shape
+        self.lo1, self.K1, self.lo2, self.K2 = int(lo1), int(K1), int(lo2), int(K2)
+        self.c1, self.c2 = census(self.img1, win), census(self.img2, win)
+        self.geo = FlowGeo(self.H, self.W, self.lo1, self.K1, self.lo2, self.K2, win * win - 1,
+                           _p(self.c1, u32p), _p(self.c2, u32p))
+
+    def projected_costs(self):
+        p1 = np.zeros((self.H, self.W, self.K1), dtype=np.int32)
+        p2 = np.zeros((self.H, self.W, self.K2), dtype=np.int32)
+        _chk(lib().or_flow_cost_projected(ctypes.byref(self.geo), _p(p1, i32p), _p(p2, i32p)),
+             "flow_cost_projected")
+        return p1, p2
+
+    def D(self, y: int, x: int, v1: float, v2: float) -> float:
+        return lib().or_flow_D(ctypes.byref(self.geo), int(y), int(x), float(v1), float(v2))
+
+    def linearise_px(self, y, x, u01, u02, h=1.0, alpha=1.0):
+        L = np.zeros(2)
+        Q = np.zeros(3)
+        box = np.zeros(4)
+        lib().or_flow_linearise_px(ctypes.byref(self.geo), int(y), int(x), float(alpha),
+                                   float(u01), float(u02), float(h), _p(L, f64p), _p(Q, f64p),
+                                   _p(box, f64p))
+        return L, Q, box
+
+    def energy(self, u1, u2, wh, wv, P: Params = Params()) -> float:
+        u1 = np.ascontiguousarray(u1, dtype=np.float64)
+        u2 = np.ascontiguousarray(u2, dtype=np.float64)
+        cp = P.cont()
+        return lib().or_flow_energy(ctypes.byref(self.geo), float(P.alpha),
+                                    _p(np.ascontiguousarray(wh, np.float64), f64p),
+                                    _p(np.ascontiguousarray(wv, np.float64), f64p),
+                                    ctypes.byref(cp), _p(u1, f64p), _p(u2, f64p))
+
+    def refine(self, u1, u2, wh, wv, iters: int, P: Params = Params(), duals=None):
+        """Primal-dual refinement from (u1, u2) (label coordinates); returns (u1, u2,
+        duals [8, H, W], energy per warp)."""
+        u1 = np.array(u1, dtype=np.float64, order="C")
+        u2 = np.array(u2, dtype=np.float64, order="C")
+        D = (np.zeros((8, self.H, self.W)) if duals is None
+             else np.array(duals, dtype=np.float64, order="C"))
+        en = np.zeros(P.warps)
+        cp = P.cont()
+        _chk(lib().or_flow_refine(ctypes.byref(self.geo), float(P.alpha),
+                                  _p(np.ascontiguousarray(wh, np.float64), f64p),
+                                  _p(np.ascontiguousarray(wv, np.float64), f64p), int(iters),
+                                  ctypes.byref(cp), _p(u1, f64p), _p(u2, f64p), _p(D, f64p),
+                                  1 if duals is None else 0, _p(en, f64p)), "flow_refine")
+        return u1, u2, D, en
+
+
+def flow_fit_samples(S, h: float = 1.0):
+    """L [2], Q [q11, q12, q22] from the 3x3 samples S[j][i] = D(u0 + (i-1)h e1 + (j-1)h e2)."""
+    S = np.ascontiguousarray(S, dtype=np.float64).reshape(9)
+    L = np.zeros(2)
+    Q = np.zeros(3)
+    lib().or_flow_fit_samples(_p(S, f64p), float(h), _p(L, f64p), _p(Q, f64p))
+    return L, Q
+
+
+def psd2(Q):
+    Q = np.array(Q, dtype=np.float64).reshape(3)
+    lib().or_psd2(_p(Q, f64p))
+    return Q
+
+
+def flow_prox(uh, u0, L, Q, box, tau):
+    L = np.ascontiguousarray(L, np.float64)
+    Q = np.ascontiguousarray(Q, np.float64)
+    box = np.ascontiguousarray(box, np.float64)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    lib().or_flow_prox(float(uh[0]), float(uh[1]), float(u0[0]), float(u0[1]), _p(L, f64p),
+                       _p(Q, f64p), _p(box, f64p), float(tau), ctypes.byref(a), ctypes.byref(b))
+    return np.array([a.value, b.value])
+
+
+def solve_flow(img1, img2, lo1: int, K1: int, lo2: int, K2: int, dmm_iters: int, pd_iters: int,
+               P: Params = Params(), nthreads: int = 0):
+    """Whole flow path: decoupled costs, Dual MM on each layer (edge weights of I1),
+    refinement of both components from the labels."""
+    fl = Flow(img1, img2, lo1, K1, lo2, K2, P.census_win)
+    p1, p2 = fl.projected_costs()
+    wh, wv = edge_weights(fl.img1, P)
+    l1, lb1, _, _ = dmm(p1, wh, wv, dmm_iters, P, nthreads=nthreads)
+    l2, lb2, _, _ = dmm(p2, wh, wv, dmm_iters, P, nthreads=nthreads)
+    u1, u2, D, en = fl.refine(l1.astype(np.float64), l2.astype(np.float64), wh, wv, pd_iters, P)
+    return dict(flow=fl, p1=p1, p2=p2, wh=wh, wv=wv, labels1=l1, labels2=l2, lb1=lb1, lb2=lb2,
+                u1=u1, u2=u2, duals=D, energy=en)
