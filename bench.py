@@ -38,13 +38,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="kitti", choices=["kitti", "diff", "stream", "batch", "lr", "minorants"],
+    ap.add_argument("--workload", default="kitti", choices=["kitti", "diff", "stream", "batch", "lr", "minorants", "flow"],
                     help="kitti: the plain method on the 1242x375x128 frame (default); "
                          "diff: forward + reverse mode of 200 PD iterations at 512x256x96; "
                          "stream: 60 warm-started frames of 1920x1080x256 (uint16 costs); "
                          "batch: 32 pairs of mixed size and label count in one CUDA graph; "
                          "lr: both views of the 1242x375x128 frame and the consistency check; "
-                         "minorants: Dual MM with the hierarchical, naive and iterative minorants")
+                         "minorants: Dual MM with the hierarchical, naive and iterative minorants; "
+                         "flow: optical flow of a 640x480 pair with 64x64 displacements")
     return ap.parse_args()
 
 
@@ -888,6 +889,122 @@ def run_minorants(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Optical flow: 640x480, displacements in [-32, 32)^2
+# ---------------------------------------------------------------------------
+
+FLOW_METRIC = "Mpixel·labels/s (optical flow, 64×64 displacements) at 640×480"
+
+
+def run_flow(args):
+    """One step = one flow: census and the two decoupled cost volumes, 10 Dual MM
+    iterations on each layer (the two layers on two streams), 100 primal-dual
+    iterations of the two-component refinement.  The metric counts the K1 x K2
+    displacements searched per pixel."""
+    import numpy as np
+    import torch
+    from paper_1601_06274_gb300 import build, dm, synthetic as S
+    build.build()
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    dev = torch.device("cuda", 0)
+    spec = S.FLOW
+    H, W = spec["H"], spec["W"]
+    lo1, K1, lo2, K2 = spec["lo1"], spec["K1"], spec["lo2"], spec["K2"]
+    NI, NP = spec["dmm_iters"], spec["pd_iters"]
+    fp = S.make_flow_workload(spec, seed=0)
+    d1_img = torch.from_numpy(fp.img1).to(dev)
+    d2_img = torch.from_numpy(fp.img2).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    f = dm.Flow(H, W, lo1, K1, lo2, K2)
+    outs = (torch.empty((H, W), dtype=torch.float32, device=dev),
+            torch.empty((H, W), dtype=torch.float32, device=dev))
+    for _ in range(args.warmup):
+        f.solve(d1_img, d2_img, NI, NP, outs)
+    torch.cuda.synchronize()
+    st = f.layer1.stream
+    l0 = f.layer1.launch_count() + f.layer2.launch_count()
+    clk = Clocks(0)
+    evs = []
+    with torch.cuda.stream(st):
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            f.solve(d1_img, d2_img, NI, NP, outs)
+            b.record(st)
+            evs.append((a, b))
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = f.layer1.launch_count() + f.layer2.launch_count() - l0
+    f.sync()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(ms)
+    units = H * W * K1 * K2
+    value = job_value(units, args.steps, 1, tot_ms)
+    d1, d2 = outs
+    inner = np.s_[40:H - 40, 40:W - 40]
+    acc = float(np.mean((np.abs(d1.cpu().numpy() - fp.gt1) < 1.0)[inner] &
+                        (np.abs(d2.cpu().numpy() - fp.gt2) < 1.0)[inner]))
+
+    # ---- stages, one at a time on the first layer's stream
+    def timed(fn, reps=3):
+        out = []
+        for r in range(reps):
+            flush.fill_(r & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            b.record(st)
+            out.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in out) / len(out)
+
+    with torch.cuda.stream(st):
+        cost_ms = timed(lambda: f.cost_volumes(d1_img, d2_img))
+        passes = {0: [], 1: []}
+        for it in range(2):
+            for which in (0, 1):
+                passes[which].append(timed(lambda: f.layer1.discrete_pass(which), 1))
+        f.cost_volumes(d1_img, d2_img)
+        f.discrete(NI)
+        refine_ms = timed(lambda: f.refine(NP, outs))
+    avg = {w: sum(v) / len(v) for w, v in passes.items()}
+    roofline = roofline_line(f.layer1, avg, H * W, K1, 1, KERNEL_NAMES)
+    roofline["stage_ms"] = {"census_and_cost_volumes": round(cost_ms, 4),
+                            "dual_mm_pass_layer1": {"horizontal": round(avg[0], 4),
+                                                    "vertical": round(avg[1], 4)},
+                            "refinement_100_iterations": round(refine_ms, 4)}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        rows = 12
+        t0 = time.perf_counter()
+        O.solve_flow(fp.img1[:rows].copy(), fp.img2[:rows].copy(), lo1, K1, lo2, K2, NI, NP,
+                     nthreads=os.cpu_count())
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": round(rows * W * K1 * K2 / t_cpu / 1e6, 4), "unit": UNIT,
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"rows 0-{rows - 1} of both frames ({W}x{rows}, {K1}x{K2} "
+                         f"displacements), the whole flow path, {t_cpu:.2f} s"}
+    line = {
+        "metric": FLOW_METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(tot_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
+        "config": {"workload": "flow-640x480x64x64", "H": H, "W": W, "d1": [lo1, lo1 + K1 - 1],
+                   "d2": [lo2, lo2 + K2 - 1], "dmm_iters": NI, "pd_iters": NP,
+                   "l2": "flushed between steps (256 MB write, outside the timed events)",
+                   "parallelism": "replicas1"},
+        "accuracy_within_1px": round(acc, 4),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": None,
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -907,6 +1024,9 @@ def main():
         return
     if args.workload == "minorants":
         run_minorants(args)
+        return
+    if args.workload == "flow":
+        run_flow(args)
         return
     import numpy as np
     import torch

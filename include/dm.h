@@ -404,6 +404,49 @@ DM_API int dm_discrete_pass_noalloc(int H, int W, int L, const dm_params* p, int
                                     const int32_t* d_lam_in, int32_t* d_lam_out,
                                     int32_t* d_err, void* stream);
 
+/* ---- Optical flow (Sec. 2.2 "Flow"; the appendix section on optical flow) --
+ *
+ * Images I1, I2 (H x W uint8); the displacement of pixel (y, x) is
+ * (d1, d2) = (lo1 + label1, lo2 + label2), d1 horizontal, with label_k in
+ * [0, K_k).  The data cost is D(d1, d2) = popcount(census1(y, x) ^ census2(y + d2,
+ * x + d1)), win*win - 1 where the displaced pixel leaves the image.  The two
+ * components are two layers, each an ordinary context: layer1 with L = K1,
+ * layer2 with L = K2, the same H, W and census window, uint8 cost storage.
+ *
+ * The discrete stage is decoupled (Eq. flow decoupled costs): layer k gets the
+ * cost min over the other component of D, and the edge weights of I1; each
+ * layer then runs dm_discrete as a stereo problem (the two may run
+ * concurrently on different streams).
+ *
+ * The continuous stage refines both components together with the quadratic
+ * model of the data term at the start of each of params.warps warps: central
+ * finite differences with step h for the gradient L and the Hessian Q of
+ * alpha * D (D bilinear between the integer displacements, arguments clamped
+ * to the ranges), Q replaced by its positive-semidefinite part; the prox is
+ * u = (I + tau Q)^-1 (u^ + tau (Q u0 - L)), each component then clamped to
+ * [u0 - h, u0 + h] within its range.  The regulariser is lambda_r omega r of
+ * each component separately.  The iterates are those of dm_refine. */
+
+/* Census of both images, edge weights of I1 and the two decoupled cost
+ * volumes (written into layer1 and layer2), on layer1's stream; layer2's
+ * stream waits for it.  Resets both layers' duals.  DM_ERR_ARG for
+ * mismatched layers or |lo| > 65535, DM_ERR_STATE without a workspace or with
+ * uint16 cost storage. */
+DM_API int dm_flow_cost_volumes(dm_ctx* layer1, dm_ctx* layer2, const uint8_t* d_img1,
+                                const uint8_t* d_img2, int lo1, int lo2);
+
+/* Bytes of caller scratch (device, 256-byte aligned) dm_flow_refine needs. */
+DM_API int dm_flow_refine_bytes(int H, int W, size_t* bytes);
+
+/* iters primal-dual iterations of the flow from the labels of the last
+ * dm_discrete of each layer (after dm_flow_cost_volumes on the same layers),
+ * on layer1's stream after the work queued on layer2's.  Writes the
+ * displacements d_u1 = lo1 + u1, d_u2 = lo2 + u2 (H x W float32, device).
+ * DM_ERR_STATE without the cost volumes or the labels, DM_ERR_WORKSPACE for a
+ * small or misaligned scratch. */
+DM_API int dm_flow_refine(dm_ctx* layer1, dm_ctx* layer2, int iters, void* d_scratch,
+                          size_t bytes, float* d_u1, float* d_u2);
+
 /* ---- Chain minorant of the Dual MM passes (Sec. 2.3 "Good and Fast
  * Minorants"; App. A) ------------------------------------------------------
  *

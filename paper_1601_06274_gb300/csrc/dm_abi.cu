@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -1274,6 +1275,139 @@ DM_API int dm_solve_lr(dm_ctx* left, dm_ctx* right, const uint8_t* d_left, const
     DM_CK(dm::launch_lr_check(al.u, ar.u, left->H, left->W, max_diff, d_ok, d_u, d_u_right,
                               left->stream));
     left->launches += 1;
+    return DM_OK;
+}
+
+// ---- optical flow ----------------------------------------------------------
+
+namespace {
+// make `later` wait for the work queued on `earlier` so far (no-op on one stream)
+int order_streams(dm_ctx* owner, cudaStream_t earlier, cudaStream_t later)
+{
+    if (earlier == later) return DM_OK;
+    if (owner->ev_fork == nullptr)
+        DM_CK(cudaEventCreateWithFlags(&owner->ev_fork, cudaEventDisableTiming));
+    DM_CK(cudaEventRecord(owner->ev_fork, earlier));
+    DM_CK(cudaStreamWaitEvent(later, owner->ev_fork, 0));
+    return DM_OK;
+}
+}  // namespace
+
+DM_API int dm_flow_cost_volumes(dm_ctx* layer1, dm_ctx* layer2, const uint8_t* d_img1,
+                                const uint8_t* d_img2, int lo1, int lo2)
+{
+    const Range range("dm_flow_cost_volumes");
+    int rc;
+    if ((rc = ready(layer1)) || (rc = ready(layer2))) return rc;
+    if (layer1 == layer2 || layer1->H != layer2->H || layer1->W != layer2->W) return DM_ERR_ARG;
+    if (d_img1 == nullptr || d_img2 == nullptr) return DM_ERR_ARG;
+    if (lo1 < -65535 || lo1 > 65535 || lo2 < -65535 || lo2 > 65535) return DM_ERR_ARG;
+    if (layer1->p.census_win != layer2->p.census_win) return DM_ERR_ARG;
+    if (layer1->cost_bytes != 1 || layer2->cost_bytes != 1) return DM_ERR_STATE;
+    const int H = layer1->H, W = layer1->W;
+    const size_t HW = (size_t)H * W;
+    const int maxc = layer1->p.census_win * layer1->p.census_win - 1;
+    uint32_t* census = reinterpret_cast<uint32_t*>(layer1->ws + layer1->lay.census);
+    cudaStream_t s1 = layer1->stream;
+    DM_CK(dm::launch_census_edges(d_img1, d_img2, H, W, layer1->p.census_win,
+                                  layer1->p.edge_threshold, layer1->p.w_hi, layer1->p.w_lo, census,
+                                  layer1->ws + layer1->lay.wh, layer1->ws + layer1->lay.wv, false,
+                                  s1));
+    DM_CK(dm::launch_flow_cost(census, census + HW, H, W, lo1, layer1->L, lo2, layer2->L, maxc,
+                               layer1->ws + layer1->lay.cost, layer2->ws + layer2->lay.cost, s1));
+    DM_CK(cudaMemcpyAsync(layer2->ws + layer2->lay.wh, layer1->ws + layer1->lay.wh, HW,
+                          cudaMemcpyDeviceToDevice, s1));
+    DM_CK(cudaMemcpyAsync(layer2->ws + layer2->lay.wv, layer1->ws + layer1->lay.wv, HW,
+                          cudaMemcpyDeviceToDevice, s1));
+    layer1->launches += 2;
+    if ((rc = order_streams(layer1, s1, layer2->stream))) return rc;
+    for (dm_ctx* c : {layer1, layer2}) {
+        c->have_cost = c->have_weights = true;
+        c->cost_f32 = nullptr;
+        c->tape_valid = false;
+        if ((rc = choose_path(c, maxc, false))) return rc;
+        if ((rc = dm_reset_duals(c))) return rc;
+    }
+    layer1->flow_partner = layer2;
+    layer1->flow_lo1 = lo1;
+    layer1->flow_lo2 = lo2;
+    return DM_OK;
+}
+
+DM_API int dm_flow_refine_bytes(int H, int W, size_t* bytes)
+{
+    if (bytes == nullptr || H <= 0 || W <= 0) return DM_ERR_ARG;
+    *bytes = (size_t)dm::kFlowArrays * align_up((size_t)H * W * sizeof(float), 256);
+    return DM_OK;
+}
+
+DM_API int dm_flow_refine(dm_ctx* layer1, dm_ctx* layer2, int iters, void* d_scratch,
+                          size_t bytes, float* d_u1, float* d_u2)
+{
+    const Range range("dm_flow_refine");
+    int rc;
+    if ((rc = ready(layer1)) || (rc = ready(layer2))) return rc;
+    if (layer1->flow_partner != layer2) return DM_ERR_STATE;
+    if (!layer1->have_labels || !layer2->have_labels) return DM_ERR_STATE;
+    if (iters < 0 || d_scratch == nullptr || d_u1 == nullptr || d_u2 == nullptr) return DM_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_scratch) & 255) != 0) return DM_ERR_WORKSPACE;
+    size_t need = 0;
+    dm_flow_refine_bytes(layer1->H, layer1->W, &need);
+    if (bytes < need) return DM_ERR_WORKSPACE;
+    const dm_params& p = layer1->p;
+    if (p.warps <= 0) return DM_ERR_ARG;
+    const int H = layer1->H, W = layer1->W;
+    const size_t HW = (size_t)H * W;
+    const size_t stride = align_up(HW * sizeof(float), 256);
+    dm::FlowArgs a{};
+    a.H = H;
+    a.W = W;
+    a.lo1 = layer1->flow_lo1;
+    a.K1 = layer1->L;
+    a.lo2 = layer1->flow_lo2;
+    a.K2 = layer2->L;
+    a.maxc = p.census_win * p.census_win - 1;
+    const uint32_t* census = reinterpret_cast<const uint32_t*>(layer1->ws + layer1->lay.census);
+    a.c1 = census;
+    a.c2 = census + HW;
+    a.wh = layer1->ws + layer1->lay.wh;
+    a.wv = layer1->ws + layer1->lay.wv;
+    a.alpha = (float)p.alpha;
+    a.lambda_r = (float)p.lambda_r;
+    a.tau = (float)p.tau;
+    a.sigma = (float)p.sigma;
+    a.h = (float)p.h;
+    a.ap = (float)p.eps;
+    a.bp = (float)p.delta;
+    a.bq = (float)(p.C + p.delta - p.eps * p.delta);
+    float* arr[dm::kFlowArrays];
+    for (int k = 0; k < dm::kFlowArrays; ++k)
+        arr[k] = reinterpret_cast<float*>(static_cast<uint8_t*>(d_scratch) + k * stride);
+    float** f[dm::kFlowArrays] = {&a.u1,  &a.u2,  &a.un1, &a.un2, &a.u01, &a.u02,
+                                  &a.L1,  &a.L2,  &a.q11, &a.q12, &a.q22, &a.b1lo,
+                                  &a.b1hi, &a.b2lo, &a.b2hi, &a.ph1, &a.pv1, &a.qh1,
+                                  &a.qv1, &a.ph2, &a.pv2, &a.qh2, &a.qv2};
+    for (int k = 0; k < dm::kFlowArrays; ++k) *f[k] = arr[k];
+    cudaStream_t s = layer1->stream;
+    if ((rc = order_streams(layer1, layer2->stream, s))) return rc;   // layer 2's labels
+    DM_CK(dm::launch_flow_init(a, reinterpret_cast<const uint16_t*>(layer1->ws + layer1->lay.labels),
+                               reinterpret_cast<const uint16_t*>(layer2->ws + layer2->lay.labels),
+                               s));
+    layer1->launches += 1;
+    const int base = iters / p.warps, extra = iters % p.warps;
+    for (int w = 0; w < p.warps; ++w) {
+        const int nit = base + (w < extra ? 1 : 0);
+        DM_CK(dm::launch_flow_lin(a, s));
+        layer1->launches += 1;
+        for (int it = 0; it < nit; ++it) {
+            DM_CK(dm::launch_flow_iter(a, s));
+            layer1->launches += 2;
+            std::swap(a.u1, a.un1);
+            std::swap(a.u2, a.un2);
+        }
+    }
+    DM_CK(dm::launch_flow_export(a, d_u1, d_u2, s));
+    layer1->launches += 1;
     return DM_OK;
 }
 

@@ -50,6 +50,10 @@ struct dm_ctx {
     // iterative run on the int32 kernel)
     int minorant = 0, max_pass = 3, gamma_num = 1, gamma_den = 4;
     bool user_weights = false;  // the current edge weights came from the caller
+    // optical flow: the partner layer and displacement offsets set by
+    // dm_flow_cost_volumes on the first layer (its census holds both images)
+    dm_ctx* flow_partner = nullptr;
+    int flow_lo1 = 0, flow_lo2 = 0;
 };
 
 namespace dm {

@@ -216,6 +216,48 @@ cudaError_t launch_census_edges(const uint8_t* left, const uint8_t* right, int H
 cudaError_t launch_cost(const uint32_t* census, int H, int W, int L, int maxc, void* cost,
                         int cost_bytes, cudaStream_t s);
 
+// flow.cu: optical flow (decoupled costs and the two-component refinement)
+struct FlowArgs {
+    int H, W, lo1, K1, lo2, K2, maxc;
+    const uint32_t* c1;      // census of image 1 [H][W]
+    const uint32_t* c2;      // census of image 2 [H][W]
+    const uint8_t* wh;
+    const uint8_t* wv;
+    float alpha, lambda_r, tau, sigma, h;
+    float ap, bp, bq;        // (alpha, beta) of R+, beta of R-
+    float* u1;               // current iterate (label coordinates)
+    float* u2;
+    float* un1;              // next iterate
+    float* un2;
+    float* u01;              // linearisation point
+    float* u02;
+    float* L1;               // gradient and PSD Hessian of the quadratic model
+    float* L2;
+    float* q11;
+    float* q12;
+    float* q22;
+    float* b1lo;             // boxes
+    float* b1hi;
+    float* b2lo;
+    float* b2hi;
+    float* ph1;              // duals of component 1 and 2
+    float* pv1;
+    float* qh1;
+    float* qv1;
+    float* ph2;
+    float* pv2;
+    float* qh2;
+    float* qv2;
+};
+constexpr int kFlowArrays = 23;  // float arrays of the refinement scratch
+cudaError_t launch_flow_cost(const uint32_t* c1, const uint32_t* c2, int H, int W, int lo1, int K1,
+                             int lo2, int K2, int maxc, uint8_t* p1, uint8_t* p2, cudaStream_t s);
+cudaError_t launch_flow_init(const FlowArgs& a, const uint16_t* lab1, const uint16_t* lab2,
+                             cudaStream_t s);
+cudaError_t launch_flow_lin(const FlowArgs& a, cudaStream_t s);
+cudaError_t launch_flow_iter(const FlowArgs& a, cudaStream_t s);
+cudaError_t launch_flow_export(const FlowArgs& a, float* d1, float* d2, cudaStream_t s);
+
 // lr.cu: two-sided consistency check of a left-view disparity and the
 // disparity of the mirrored (right-view) problem
 cudaError_t launch_lr_check(const float* ul, const float* um, int H, int W, float max_diff,

@@ -99,6 +99,9 @@ def lib() -> ctypes.CDLL:
             "dm_solve_next": [_vp, _vp, _vp, _i, _i, _vp],
             "dm_cost_volume_mirrored": [_vp, _vp, _vp],
             "dm_set_minorant": [_vp, _i, _i, _i, _i],
+            "dm_flow_cost_volumes": [_vp, _vp, _vp, _vp, _i, _i],
+            "dm_flow_refine_bytes": [_i, _i, ctypes.POINTER(ctypes.c_size_t)],
+            "dm_flow_refine": [_vp, _vp, _i, _vp, ctypes.c_size_t, _vp, _vp],
             "dm_lr_check": [_vp, _vp, _i, _i, ctypes.c_float, _vp, _vp, _vp, _vp],
             "dm_solve_lr": [_vp, _vp, _vp, _vp, _i, _i, ctypes.c_float, _vp, _vp, _vp],
             "dm_set_data_weights": [_vp, _vp],
@@ -609,6 +612,68 @@ class StereoLR:
     def sync(self):
         self.left.sync()
         self.right.sync()
+
+
+class Flow:
+    """Optical flow (dm_flow_*): two layer contexts, the second on its own stream
+    so that the two discrete stages run concurrently, and the refinement
+    scratch.  Displacement d_k = lo_k + label_k, label_k in [0, K_k)."""
+
+    def __init__(self, H: int, W: int, lo1: int, K1: int, lo2: int, K2: int,
+                 params: DmParams | None = None, device: str = "cuda"):
+        import torch
+        self._torch = torch
+        self.H, self.W = H, W
+        self.lo1, self.K1, self.lo2, self.K2 = lo1, K1, lo2, K2
+        self.device = torch.device(device)
+        self.layer1 = Context(H, W, K1, params, device)
+        self.layer2 = Context(H, W, K2, params, device, stream=torch.cuda.Stream(self.device))
+        nb = ctypes.c_size_t()
+        _ck(lib().dm_flow_refine_bytes(H, W, ctypes.byref(nb)), "dm_flow_refine_bytes")
+        self.scratch_bytes = nb.value
+        self._scratch = torch.empty(self.scratch_bytes, dtype=torch.uint8, device=self.device)
+
+    def cost_volumes(self, img1, img2):
+        l1 = self.layer1
+        self._i1, self._i2 = l1._dev_u8(img1), l1._dev_u8(img2)
+        _ck(lib().dm_flow_cost_volumes(l1._h, self.layer2._h, self._i1.data_ptr(),
+                                       self._i2.data_ptr(), int(self.lo1), int(self.lo2)),
+            "dm_flow_cost_volumes")
+
+    def discrete(self, iters: int, lower_bounds: bool = False):
+        b1 = self.layer1.discrete(iters, lower_bounds)
+        b2 = self.layer2.discrete(iters, lower_bounds)
+        return (b1, b2) if lower_bounds else None
+
+    def refine(self, iters: int, outs=None):
+        """(d1, d2) float32 [H, W] displacements after `iters` iterations."""
+        t = self._torch
+        d1, d2 = outs if outs is not None else (
+            t.empty((self.H, self.W), dtype=t.float32, device=self.device),
+            t.empty((self.H, self.W), dtype=t.float32, device=self.device))
+        _ck(lib().dm_flow_refine(self.layer1._h, self.layer2._h, int(iters),
+                                 self._scratch.data_ptr(), self.scratch_bytes, d1.data_ptr(),
+                                 d2.data_ptr()), "dm_flow_refine")
+        return d1, d2
+
+    def solve(self, img1, img2, dmm_iters: int, pd_iters: int, outs=None):
+        self.cost_volumes(img1, img2)
+        self.discrete(dmm_iters)
+        return self.refine(pd_iters, outs)
+
+    def sync(self):
+        self.layer1.sync()
+        self.layer2.sync()
+
+
+def solve_flow(img1, img2, lo1: int, K1: int, lo2: int, K2: int, dmm_iters: int = 10,
+               pd_iters: int = 100, params: DmParams | None = None, device: str = "cuda"):
+    """Optical flow of one pair: (d1, d2) float32 displacements [H, W]."""
+    H, W = np.asarray(img1).shape if isinstance(img1, np.ndarray) else tuple(img1.shape)
+    f = Flow(H, W, lo1, K1, lo2, K2, params, device)
+    out = f.solve(img1, img2, dmm_iters, pd_iters)
+    f.sync()
+    return out
 
 
 def lr_check(u_left, u_mirrored, max_diff: float = 1.0, outs=None):

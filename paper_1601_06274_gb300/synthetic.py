@@ -203,6 +203,62 @@ def batch_specs(n_pairs: int = 32, seed: int = 0) -> list[dict]:
     return out
 
 
+@dataclass
+class FlowPair:
+    img1: np.ndarray        # uint8 [H, W]
+    img2: np.ndarray        # uint8 [H, W]
+    gt1: np.ndarray         # int64 [H, W], horizontal displacement of every img1 pixel
+    gt2: np.ndarray         # int64 [H, W], vertical displacement
+    seed: int
+
+
+def make_flow_pair(H: int, W: int, lo1: int, K1: int, lo2: int, K2: int, *, objects: int = 6,
+                   noise_sigma: float = 2.0, seed: int = 0) -> FlowPair:
+    """Two frames of a moving scene: a textured background displaced by one integer
+    vector and `objects` textured rectangles on top, each displaced by its own
+    (later rectangles occlude earlier ones, in both frames).  Every displacement
+    lies in [lo1, lo1 + K1) x [lo2, lo2 + K2); img2(y + d2, x + d1) = img1(y, x)
+    wherever that pixel stays visible; uncovered img2 pixels show fresh texture
+    and img2 gets N(0, noise_sigma^2) noise."""
+    rng = np.random.default_rng(seed)
+    M = max(abs(lo1), abs(lo1 + K1 - 1), abs(lo2), abs(lo2 + K2 - 1)) + 1
+    canvas = _texture(rng, H + 2 * M, W + 2 * M)
+    draw = lambda: (int(rng.integers(lo1, lo1 + K1)), int(rng.integers(lo2, lo2 + K2)))
+    b1, b2 = draw()
+    img1 = canvas[M:M + H, M:M + W].copy()
+    ys, xs = np.mgrid[0:H, 0:W]
+    img2 = canvas[np.clip(ys - b2 + M, 0, H + 2 * M - 1), np.clip(xs - b1 + M, 0, W + 2 * M - 1)]
+    gt1 = np.full((H, W), b1, dtype=np.int64)
+    gt2 = np.full((H, W), b2, dtype=np.int64)
+    for _ in range(objects):
+        h = min(H, int(rng.integers(max(4, H // 10), max(5, H // 3))))
+        w = min(W, int(rng.integers(max(4, W // 10), max(5, W // 3))))
+        y0 = int(rng.integers(0, max(1, H - h)))
+        x0 = int(rng.integers(0, max(1, W - w)))
+        f1, f2 = draw()
+        patch = _texture(rng, h, w)
+        img1[y0:y0 + h, x0:x0 + w] = patch
+        gt1[y0:y0 + h, x0:x0 + w] = f1
+        gt2[y0:y0 + h, x0:x0 + w] = f2
+        ya, xa = max(0, y0 + f2), max(0, x0 + f1)
+        yb, xb = min(H, y0 + f2 + h), min(W, x0 + f1 + w)
+        if ya < yb and xa < xb:
+            img2[ya:yb, xa:xb] = patch[ya - y0 - f2:yb - y0 - f2, xa - x0 - f1:xb - x0 - f1]
+    noise = np.rint(rng.normal(0.0, noise_sigma, size=(H, W))).astype(np.int64)
+    img2 = np.clip(img2.astype(np.int64) + noise, 0, 255).astype(np.uint8)
+    return FlowPair(img1=img1, img2=img2, gt1=gt1, gt2=gt2, seed=seed)
+
+
+# 640x480 frames (the paper's live camera size) with displacements in [-32, 32)^2
+FLOW = dict(H=480, W=640, lo1=-32, K1=64, lo2=-32, K2=64, objects=6, noise_sigma=2.0,
+            dmm_iters=10, pd_iters=100)
+
+
+def make_flow_workload(spec: dict, seed: int = 0) -> FlowPair:
+    return make_flow_pair(spec["H"], spec["W"], spec["lo1"], spec["K1"], spec["lo2"], spec["K2"],
+                          objects=spec["objects"], noise_sigma=spec["noise_sigma"], seed=seed)
+
+
 def random_image(H: int, W: int, seed: int) -> np.ndarray:
     """Plain uniform uint8 noise (edge-case tests)."""
     return np.random.default_rng(seed).integers(0, 256, size=(H, W), dtype=np.uint8)

@@ -218,3 +218,20 @@ def test_set_minorant_checks_arguments_without_gpu(lib):
         assert lib.dm_set_minorant(h, *args) == dm.DM_ERR_ARG, args
     assert lib.dm_set_minorant(None, 0, 0, 0, 0) == dm.DM_ERR_ARG
     lib.dm_destroy(h)
+
+
+def test_flow_calls_check_arguments_without_gpu(lib):
+    from paper_1601_06274_gb300 import dm
+    p = dm.default_params()
+    a, b = ctypes.c_void_p(), ctypes.c_void_p()
+    assert lib.dm_create(8, 8, 16, ctypes.byref(p), ctypes.byref(a)) == 0
+    assert lib.dm_create(8, 8, 8, ctypes.byref(p), ctypes.byref(b)) == 0
+    fake = ctypes.c_void_p(4096)
+    n = ctypes.c_size_t()
+    assert lib.dm_flow_refine_bytes(8, 8, ctypes.byref(n)) == 0 and n.value >= 23 * 8 * 8 * 4
+    assert lib.dm_flow_refine_bytes(0, 8, ctypes.byref(n)) == dm.DM_ERR_ARG
+    assert lib.dm_flow_cost_volumes(a, b, fake, fake, -2, -2) == dm.DM_ERR_STATE   # no workspace
+    assert lib.dm_flow_cost_volumes(None, b, fake, fake, -2, -2) == dm.DM_ERR_ARG
+    assert lib.dm_flow_refine(a, b, 10, fake, 1 << 20, fake, fake) == dm.DM_ERR_STATE
+    lib.dm_destroy(a)
+    lib.dm_destroy(b)
