@@ -42,3 +42,17 @@ def test_api_walkthrough():
     assert torch.equal(s0, u)   # uint16 storage of the same costs gives the same result
     s1 = sctx.solve_next(pair.left, pair.right, 10, 100)
     assert s1.shape == (H, W)
+
+    u_chk, ok, u_left, u_right = dm.solve_lr(pair.left, pair.right, L=L, dmm_iters=10,
+                                             pd_iters=100)
+    assert torch.equal(u_left, u) and ok.dtype == torch.uint8 and u_right.shape == (H, W)
+
+    ctx.set_minorant("iterative", max_pass=3, gamma=(1, 4))
+    ctx.cost_volume(pair.left, pair.right)
+    lb_it = ctx.discrete(3, lower_bounds=True)
+    assert ctx.path()[0] == 32 and lb_it.shape == (3,)
+
+    fp = synthetic.make_flow_workload(synthetic.FLOW)
+    d1, d2 = dm.solve_flow(fp.img1, fp.img2, lo1=-32, K1=64, lo2=-32, K2=64, dmm_iters=10,
+                           pd_iters=100)
+    assert d1.shape == (480, 640) and bool(torch.isfinite(d2).all())
