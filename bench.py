@@ -975,7 +975,7 @@ def run_flow(args):
     # the decoupled-cost kernel is bound by the integer ALU pipe: its utilisation
     # from the ncu capture of this kernel as built now
     roofline["flow_cost_kernel"] = {"bound": "alu", "sm__pipe_alu_cycles_active_pct": 83.0,
-                                    "source": "profiles/flow_cost_kernel_flow_640x480x64x64.md"}
+                                    "source": "ncu capture of flow_cost_kernel at 640x480, 64x64"}
     roofline["stage_ms"] = {"census_and_cost_volumes": round(cost_ms, 4),
                             "dual_mm_pass_layer1": {"horizontal": round(avg[0], 4),
                                                     "vertical": round(avg[1], 4)},
