@@ -376,6 +376,122 @@ int or_iterative_minorant(int n, int K, const i64* theta, const i64* V, int max_
     return OR_OK;
 }
 
+/* Minimum of the chain (theta, V) and a minimiser (plain forward recursion with
+ * back-pointers, Eq. msg-pass); x may be NULL. */
+static double chain_viterbi(int n, int K, const double* theta, const i64* V, int* x)
+{
+    double* best = (double*)malloc((size_t)n * K * sizeof(double));
+    int* arg = (int*)malloc((size_t)n * K * sizeof(int));
+    for (int l = 0; l < K; ++l) best[l] = theta[l];
+    for (int k = 1; k < n; ++k)
+        for (int b = 0; b < K; ++b) {
+            double m = INFINITY;
+            int am = 0;
+            for (int a = 0; a < K; ++a) {
+                double v = best[(i64)(k - 1) * K + a] + (double)V[(i64)(k - 1) * K + (a > b ? a - b : b - a)];
+                if (v < m) { m = v; am = a; }
+            }
+            best[(i64)k * K + b] = m + theta[(i64)k * K + b];
+            arg[(i64)k * K + b] = am;
+        }
+    double m = INFINITY;
+    int l_end = 0;
+    for (int l = 0; l < K; ++l)
+        if (best[(i64)(n - 1) * K + l] < m) { m = best[(i64)(n - 1) * K + l]; l_end = l; }
+    if (x) {
+        x[n - 1] = l_end;
+        for (int k = n - 1; k > 0; --k) x[k - 1] = arg[(i64)k * K + x[k]];
+    }
+    free(best);
+    free(arg);
+    return m;
+}
+
+/* Maximal uniform minorant (Alg. uniform-minorant; reading R38).  lam := 0;
+ * repeat: min-marginals m of f - lam; stop when all vanish (|m| <= tol);
+ * O = [m <= tol]; eps = min over labellings x with <1-O, x> > 0 of
+ * (f - lam)(x) / <1-O, x>, the minimum ratio path of Lawler's method, found by
+ * Dinkelbach's parametric iteration (a Viterbi pass of f - lam - eps (1-O) per
+ * step); lam += eps (1-O).  Double precision; returns the number of rounds
+ * (or -1 without convergence within max_rounds). */
+int or_uniform_minorant(int n, int K, const i64* theta, const i64* V, double tol, int max_rounds,
+                        double* lam)
+{
+    double* rem = (double*)malloc((size_t)n * K * sizeof(double));   /* theta - lam */
+    double* t2 = (double*)malloc((size_t)n * K * sizeof(double));
+    double* left = (double*)malloc((size_t)n * K * sizeof(double));
+    double* right = (double*)malloc((size_t)n * K * sizeof(double));
+    double* mm = (double*)malloc((size_t)n * K * sizeof(double));
+    int* O = (int*)malloc((size_t)n * K * sizeof(int));
+    int* x = (int*)malloc((size_t)n * sizeof(int));
+    int rounds = -1;
+    for (i64 e = 0; e < (i64)n * K; ++e) lam[e] = 0.0;
+    for (int r = 0; r < max_rounds; ++r) {
+        for (i64 e = 0; e < (i64)n * K; ++e) rem[e] = (double)theta[e] - lam[e];
+        /* min-marginals of the remainder (Eq. min-marg-expression) */
+        for (int l = 0; l < K; ++l) { left[l] = 0.0; right[(i64)(n - 1) * K + l] = 0.0; }
+        for (int k = 1; k < n; ++k)
+            for (int b = 0; b < K; ++b) {
+                double m = INFINITY;
+                for (int a = 0; a < K; ++a) {
+                    double v = left[(i64)(k - 1) * K + a] + rem[(i64)(k - 1) * K + a] +
+                               (double)V[(i64)(k - 1) * K + (a > b ? a - b : b - a)];
+                    if (v < m) m = v;
+                }
+                left[(i64)k * K + b] = m;
+            }
+        for (int k = n - 2; k >= 0; --k)
+            for (int a = 0; a < K; ++a) {
+                double m = INFINITY;
+                for (int b = 0; b < K; ++b) {
+                    double v = right[(i64)(k + 1) * K + b] + rem[(i64)(k + 1) * K + b] +
+                               (double)V[(i64)k * K + (a > b ? a - b : b - a)];
+                    if (v < m) m = v;
+                }
+                right[(i64)k * K + a] = m;
+            }
+        int all_zero = 1;
+        for (i64 e = 0; e < (i64)n * K; ++e) {
+            mm[e] = left[e] + rem[e] + right[e];
+            O[e] = fabs(mm[e]) <= tol;
+            if (!O[e]) all_zero = 0;
+        }
+        if (all_zero) { rounds = r; break; }
+        /* Dinkelbach: start from the ratio of a minimiser of f - lam that uses a
+         * label outside O (one exists: some min-marginal is positive) */
+        double eps = INFINITY;
+        {
+            /* the labelling that takes, at the first node with a non-optimal label,
+             * that label and the best completion: its ratio is finite */
+            for (i64 e = 0; e < (i64)n * K; ++e) t2[e] = rem[e] - (O[e] ? 0.0 : 1e6);
+            chain_viterbi(n, K, t2, V, x);
+            double A = 0.0, Bc = 0.0;
+            for (int k = 0; k < n; ++k) {
+                A += rem[(i64)k * K + x[k]];
+                Bc += O[(i64)k * K + x[k]] ? 0.0 : 1.0;
+                if (k + 1 < n) A += (double)V[(i64)k * K + (x[k] > x[k + 1] ? x[k] - x[k + 1] : x[k + 1] - x[k])];
+            }
+            eps = A / Bc;
+        }
+        for (int it = 0; it < 200; ++it) {
+            for (i64 e = 0; e < (i64)n * K; ++e) t2[e] = rem[e] - (O[e] ? 0.0 : eps);
+            double v = chain_viterbi(n, K, t2, V, x);
+            if (v >= -tol) break;   /* min_x A - eps B = 0: eps is the minimum ratio */
+            double A = 0.0, Bc = 0.0;
+            for (int k = 0; k < n; ++k) {
+                A += rem[(i64)k * K + x[k]];
+                Bc += O[(i64)k * K + x[k]] ? 0.0 : 1.0;
+                if (k + 1 < n) A += (double)V[(i64)k * K + (x[k] > x[k + 1] ? x[k] - x[k + 1] : x[k + 1] - x[k])];
+            }
+            eps = A / Bc;
+        }
+        for (i64 e = 0; e < (i64)n * K; ++e)
+            if (!O[e]) lam[e] += eps;
+    }
+    free(rem); free(t2); free(left); free(right); free(mm); free(O); free(x);
+    return rounds;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Dual MM (Alg. Dual_MM) on the 4-connected grid split into horizontal      */
 /* chains f (data cost + horizontal edges) and vertical chains g (vertical    */
@@ -515,6 +631,92 @@ int or_dmm(int H, int W, int L, const int32_t* cost, const int32_t* wh, const in
 {
     return or_dmm_kind(H, W, L, cost, wh, wv, eps, delta, C, iters, lam_h, lam_v, lb, labels,
                        nthreads, 0, 1, 1, 1);
+}
+
+/* Primal_MM (Alg. Primal_MM) on the grid split into horizontal chains f (data
+ * and horizontal edges) and vertical chains g.  The modular majorant of a chain
+ * exact at the current labelling xk (reading R39): every edge (i, j) charges
+ * omega C (the cap of its truncated penalty) to each end whose label leaves xk,
+ * and splits its current cost f_ij(xk_i, xk_j) evenly between the two ends;
+ * since 0 <= f_ij <= omega C this is >= f_ij everywhere and equal at xk.
+ * One iteration: majorise f at xk, minimise the vertical chains g + f_bar;
+ * majorise g at the result, minimise the horizontal chains f + g_bar.
+ * labels: the start on entry, the result on exit; energy[t] after iteration t. */
+i64 or_discrete_energy(int H, int W, int L, const int32_t* cost, const int32_t* wh,
+                       const int32_t* wv, double eps, double delta, double C,
+                       const uint16_t* labels);
+
+int or_primal_mm(int H, int W, int L, const int32_t* cost, const int32_t* wh, const int32_t* wv,
+                 double eps, double delta, double C, int iters, uint16_t* labels, i64* energy)
+{
+    if (H <= 0 || W <= 0 || L <= 0 || iters < 0) return OR_ERR_ARG;
+    or_tables Th, Tv;
+    int rc = build_tables(&Th, L, wh, H * W, eps, delta, C);
+    if (!rc) rc = build_tables(&Tv, L, wv, H * W, eps, delta, C);
+    if (rc) { free_tables(&Th); return rc; }
+    const int n = H > W ? H : W;
+    double* theta = (double*)malloc((size_t)n * L * sizeof(double));
+    i64* V = (i64*)malloc((size_t)n * L * sizeof(i64));
+    int* x = (int*)malloc((size_t)n * sizeof(int));
+    double* bar = (double*)malloc((size_t)H * W * L * sizeof(double));
+    for (int t = 0; t < iters; ++t) {
+        for (int half = 0; half < 2; ++half) {
+            /* half 0: majorise f (horizontal edges + data), minimise columns of g + f_bar;
+             * half 1: majorise g (vertical edges), minimise rows of f + g_bar */
+            for (int y = 0; y < H; ++y)
+                for (int xx = 0; xx < W; ++xx) {
+                    i64 p = (i64)y * W + xx;
+                    for (int l = 0; l < L; ++l) {
+                        double v = half == 0 ? (double)cost[p * L + l] : 0.0;
+                        bar[p * L + l] = v;
+                    }
+                }
+            for (int y = 0; y < H; ++y)
+                for (int xx = 0; xx < W; ++xx) {
+                    i64 p = (i64)y * W + xx;
+                    int has = half == 0 ? xx + 1 < W : y + 1 < H;
+                    if (!has) continue;
+                    i64 q = half == 0 ? p + 1 : p + W;
+                    int om = half == 0 ? wh[p] : wv[p];
+                    const i64* tab = find_table(half == 0 ? &Th : &Tv, om);
+                    double cap = (double)tab[L - 1 < 0 ? 0 : L - 1];
+                    for (int d = 0; d < L; ++d) if ((double)tab[d] > cap) cap = (double)tab[d];
+                    int a = labels[p], b = labels[q];
+                    double cur = (double)tab[a > b ? a - b : b - a];
+                    for (int l = 0; l < L; ++l) {
+                        bar[p * L + l] += 0.5 * cur + (l != a ? cap : 0.0);
+                        bar[q * L + l] += 0.5 * cur + (l != b ? cap : 0.0);
+                    }
+                }
+            /* minimise the other family of chains plus the modular majorant */
+            int nch = half == 0 ? W : H, len = half == 0 ? H : W;
+            for (int c = 0; c < nch; ++c) {
+                for (int k = 0; k < len; ++k) {
+                    int y = half == 0 ? k : c, xx = half == 0 ? c : k;
+                    i64 p = (i64)y * W + xx;
+                    for (int l = 0; l < L; ++l) {
+                        double v = bar[p * L + l];
+                        if (half == 1) v += (double)cost[p * L + l];
+                        theta[(i64)k * L + l] = v;
+                    }
+                    if (k + 1 < len) {
+                        int om = half == 0 ? wv[p] : wh[p];
+                        memcpy(V + (i64)k * L, find_table(half == 0 ? &Tv : &Th, om),
+                               (size_t)L * sizeof(i64));
+                    }
+                }
+                chain_viterbi(len, L, theta, V, x);
+                for (int k = 0; k < len; ++k) {
+                    int y = half == 0 ? k : c, xx = half == 0 ? c : k;
+                    labels[(i64)y * W + xx] = (uint16_t)x[k];
+                }
+            }
+        }
+        if (energy) energy[t] = or_discrete_energy(H, W, L, cost, wh, wv, eps, delta, C, labels);
+    }
+    free(theta); free(V); free(x); free(bar);
+    free_tables(&Th); free_tables(&Tv);
+    return OR_OK;
 }
 
 /* Discrete energy, Eq. (energy-pairwise) with the stereo terms of Sec. 2.2. */

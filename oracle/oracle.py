@@ -94,6 +94,10 @@ def lib():
         L.or_naive_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
         L.or_iterative_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p] + \
             [ctypes.c_int] * 3 + [i64p]
+        L.or_uniform_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, ctypes.c_double,
+                                          ctypes.c_int, f64p]
+        L.or_primal_mm.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
+                                   + [ctypes.c_int, u16p, i64p])
         L.or_dmm_pass_kind.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p]
                                        + [ctypes.c_double] * 3 + [ctypes.c_int, i64p, i64p]
                                        + [ctypes.c_int] * 5)
@@ -282,6 +286,31 @@ def iterative_minorant(theta: np.ndarray, V: np.ndarray, max_pass: int = 3,
                                      int(gamma[0]), int(gamma[1]), _p(out, i64p)),
          "iterative_minorant")
     return out
+
+
+def uniform_minorant(theta: np.ndarray, V: np.ndarray, tol: float = 1e-9,
+                     max_rounds: int = 10000):
+    """Alg. uniform-minorant (minimum ratios by Dinkelbach's iteration), float64;
+    returns (lam, rounds)."""
+    theta, V, n, K = _chain_args(theta, V)
+    out = np.zeros((n, K), dtype=np.float64)
+    r = lib().or_uniform_minorant(n, K, _p(theta, i64p), _p(V, i64p), float(tol), int(max_rounds),
+                                  _p(out, f64p))
+    if r < 0:
+        raise RuntimeError("oracle uniform_minorant did not converge")
+    return out, r
+
+
+def primal_mm(cost, wh, wv, iters: int, labels0, P: Params = Params()):
+    """Alg. Primal_MM from labels0; returns (labels, energy after each iteration)."""
+    cost = np.ascontiguousarray(cost, dtype=np.int32)
+    H, W, L = cost.shape
+    labels = np.array(labels0, dtype=np.uint16, order="C")
+    en = np.zeros(max(iters, 1), dtype=np.int64)
+    _chk(lib().or_primal_mm(H, W, L, _p(cost, i32p), _p(np.ascontiguousarray(wh, np.int32), i32p),
+                            _p(np.ascontiguousarray(wv, np.int32), i32p), P.eps, P.delta, P.C,
+                            int(iters), _p(labels, u16p), _p(en, i64p)), "primal_mm")
+    return labels, en[:iters]
 
 
 MINORANTS = {"hier": 0, "naive": 1, "iterative": 2}
