@@ -11,6 +11,12 @@
  *   3. non-linear primal-dual refinement           (Sec. 2.4, Eq. cont_iterates;
  *                                                   Sec. 3.1 data term and prox)
  *
+ * and, around it: a batched form (many pairs, persistent kernels, one CUDA
+ * graph), a differentiable form of the refinement, a streaming form (uint16
+ * costs, warm start), the two-sided consistency check (Sec. 4.1.1), the naive
+ * and iterative chain minorants (Sec. 2.3, App. A) and optical flow with
+ * decoupled layers (Sec. 2.2 "Flow").
+ *
  * Conventions shared by every entry point
  *   - Images are H x W, row-major, uint8, one byte per pixel (no padding).
  *   - The cost volume is [H][W][L] uint8 (uint16 with params.cost_bytes = 2),
