@@ -382,6 +382,13 @@ DM_API int dm_batch_get_tuning(const dm_batch* b, int* choice);
 /* Kernels enqueued for the batch (a replay counts the graph's kernels). */
 DM_API int dm_batch_launch_count(const dm_batch* b, uint64_t* count);
 
+/* One Dual MM pass (which = 0 horizontal, 1 vertical) over every pair of a
+ * batch that has been solved or captured before, with the persistent kernels
+ * of the solve, on the batch's stream; for instrumentation.  It continues from
+ * the current duals and adds the pass's bound to the first lower-bound slot.
+ * DM_ERR_STATE before the first solve or capture. */
+DM_API int dm_batch_discrete_pass(dm_batch* b, int which);
+
 /* Allocation-free variant of dm_discrete_pass.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
  * (a fixed memory budget decided at start-up, a real-time or embedded

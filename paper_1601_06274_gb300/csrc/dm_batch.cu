@@ -655,6 +655,17 @@ DM_API int dm_batch_sync(dm_batch* b)
     return DM_OK;
 }
 
+DM_API int dm_batch_discrete_pass(dm_batch* b, int which)
+{
+    if (b == nullptr || (which != 0 && which != 1)) return DM_ERR_ARG;
+    if (!b->prepared || b->ws == nullptr) return DM_ERR_STATE;
+    for (const Group& g : b->groups) {
+        int rc = batch_pass(b, g, which, 0, false);
+        if (rc) return rc;
+    }
+    return DM_OK;
+}
+
 DM_API int dm_batch_launch_count(const dm_batch* b, uint64_t* count)
 {
     if (b == nullptr || count == nullptr) return DM_ERR_ARG;

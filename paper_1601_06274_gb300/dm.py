@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
             "dm_batch_set_tuning": [_vp, _vp],
             "dm_batch_get_tuning": [_vp, _vp],
             "dm_batch_launch_count": [_vp, ctypes.POINTER(ctypes.c_uint64)],
+            "dm_batch_discrete_pass": [_vp, _i],
             "dm_discrete_pass_noalloc": [_i, _i, _i, ctypes.POINTER(DmParams), _i, _vp, _vp,
                                          _vp, _vp, _vp, _vp],
             "dm_set_cost_volume_f32": [_vp, _vp, _vp, _vp],
@@ -571,6 +572,10 @@ class Batch:
         n = ctypes.c_uint64()
         _ck(lib().dm_batch_launch_count(self._h, ctypes.byref(n)), "dm_batch_launch_count")
         return n.value
+
+    def discrete_pass(self, which: int):
+        """One Dual MM pass over every pair (instrumentation; after a solve)."""
+        _ck(lib().dm_batch_discrete_pass(self._h, int(which)), "dm_batch_discrete_pass")
 
 
 class StereoLR:

@@ -235,3 +235,18 @@ def test_flow_calls_check_arguments_without_gpu(lib):
     assert lib.dm_flow_refine(a, b, 10, fake, 1 << 20, fake, fake) == dm.DM_ERR_STATE
     lib.dm_destroy(a)
     lib.dm_destroy(b)
+
+
+def test_batch_discrete_pass_needs_a_solve(lib):
+    from paper_1601_06274_gb300 import dm
+    p = dm.default_params()
+    n = 2
+    H = (ctypes.c_int * n)(8, 12)
+    W = (ctypes.c_int * n)(16, 20)
+    L = (ctypes.c_int * n)(16, 32)
+    b = ctypes.c_void_p()
+    assert lib.dm_batch_create(n, H, W, L, ctypes.byref(p), ctypes.byref(b)) == 0
+    assert lib.dm_batch_discrete_pass(b, 0) == dm.DM_ERR_STATE
+    assert lib.dm_batch_discrete_pass(b, 2) == dm.DM_ERR_ARG
+    assert lib.dm_batch_discrete_pass(None, 0) == dm.DM_ERR_ARG
+    lib.dm_batch_destroy(b)

@@ -74,6 +74,24 @@ def test_batch_after_work_still_queued_on_torch_stream(dm):
     torch.cuda.synchronize()
 
 
+def test_batch_discrete_pass_continues_every_pair(dm):
+    """After a 3-iteration solve, one more horizontal pass over the batch gives
+    every pair the oracle's next horizontal pass."""
+    shapes = SMALL[:5]
+    pairs = _pairs(shapes, 600)
+    b = dm.Batch(shapes)
+    b.solve([p.left for p in pairs], [p.right for p in pairs], 3, 0)
+    b.discrete_pass(0)
+    b.sync()
+    for k, ((H, W, L), sp) in enumerate(zip(shapes, pairs)):
+        cost = O.cost_volume(sp.left, sp.right, L)
+        wh, wv = O.edge_weights(sp.left)
+        _, _, _, lam_v = O.dmm(cost, wh, wv, 3)
+        ref = O.dmm_pass(cost, wh, wv, 0, lam_v)
+        lh, _ = b.pairs[k].duals()
+        assert np.array_equal(lh.cpu().numpy().astype(np.int64), ref), k
+
+
 def test_batch_graph_replays_new_inputs(dm):
     import torch
     shapes = SMALL[:6]
