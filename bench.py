@@ -195,7 +195,7 @@ def run_diff(args):
     stream = ctx.stream
     ctx.cost_volume(sp.left, sp.right)
     ctx.discrete(10)
-    c8, _, _ = ctx.cost()
+    c8, wh_t, wv_t = ctx.cost()
     g = torch.Generator(device=dev).manual_seed(rank)
     cost = (c8.float() + torch.rand(c8.shape, device=dev, generator=g)).contiguous()
     alpha = (0.5 + torch.rand((H, W), device=dev, generator=g)).contiguous()
@@ -289,6 +289,24 @@ def run_diff(args):
     if os.path.exists(peaks_path):
         peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
     achieved = PD_ADJ_BYTES * H * W / (adj_it_ms / 1e3) / 1e9
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # the oracle's reverse mode on the first rows of the same inputs
+        from oracle import oracle as O
+        rows = 32
+        wh_c = wh_t[:rows].cpu().numpy().astype(np.float64)
+        wv_c = wv_t[:rows].cpu().numpy().astype(np.float64)
+        wv_c[-1, :] = 0.0
+        u0_c = dm.labels_u16(ctx.labels())[:rows].astype(np.float64)
+        t0 = time.perf_counter()
+        O.refine_grad(cost[:rows].double().cpu().numpy(), wh_c, wv_c, u0_c, NP,
+                      gt[:rows].double().cpu().numpy(), O.Params(),
+                      alpha=alpha[:rows].double().cpu().numpy())
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": round(rows * W * L / t_cpu / 1e6, 4), "unit": "Mpixel·labels/s",
+               "cores": 1, "kind": "oracle",
+               "sample": f"rows 0-{rows - 1} ({W}x{rows}x{L}), forward and reverse of {NP} "
+                         f"iterations in FP64, {t_cpu:.2f} s"}
     line = {
         "metric": DIFF_METRIC, "value": round(value, 3), "unit": "Mpixel·labels/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -307,7 +325,7 @@ def run_diff(args):
                      "peak_source": peak_src,
                      "fwd_iter_us": round(fwd_it_ms * 1e3, 3),
                      "adj_iter_us": round(adj_it_ms * 1e3, 3)},
-        "cpu_baseline": None,
+        "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 3), "unit": "Mpixel·labels/s",
                 "h2d_bytes_per_step": 4 * H * W * L + 4 * H * W,
                 "d2h_bytes_per_step": 4 * H * W * L},
@@ -972,6 +990,25 @@ def run_flow(args):
     tot_ms = sum(ms)
     units = H * W * K1 * K2
     value = job_value(units, args.steps, 1, tot_ms)
+    # ---- end to end: pinned host frames in, both displacement fields back
+    h1 = torch.from_numpy(fp.img1).pin_memory()
+    h2 = torch.from_numpy(fp.img2).pin_memory()
+    hd1 = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    hd2 = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    e_ms = []
+    with torch.cuda.stream(st):
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            o1, o2 = f.solve(h1, h2, NI, NP, outs)
+            hd1.copy_(o1, non_blocking=True)
+            hd2.copy_(o2, non_blocking=True)
+            b.record(st)
+            torch.cuda.synchronize()
+            e_ms.append(a.elapsed_time(b))
+    e2e_value = units * args.steps / (sum(e_ms) / 1e3) / 1e6
     d1, d2 = outs
     inner = np.s_[40:H - 40, 40:W - 40]
     acc = float(np.mean((np.abs(d1.cpu().numpy() - fp.gt1) < 1.0)[inner] &
@@ -1032,7 +1069,9 @@ def run_flow(args):
                    "l2": "flushed between steps (256 MB write, outside the timed events)",
                    "parallelism": "replicas1"},
         "accuracy_within_1px": round(acc, 4),
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": None,
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 2 * H * W,
+                "d2h_bytes_per_step": 8 * H * W},
         "gpu_launches": launches, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
