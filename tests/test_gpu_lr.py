@@ -188,3 +188,17 @@ def test_solve_lr_full_frame(dm):
     ok_g, out_g = O.lr_check(_np(u1), _np(ur), 1.0)
     assert np.array_equal(_np(ok), ok_g) and np.array_equal(_np(u), out_g)
     assert ok_g.mean() > 0.8
+
+
+def test_solve_lr_with_uint16_costs(dm):
+    """Two views with uint16 cost storage give the same result as uint8."""
+    H, W, L = 20, 36, 32
+    sp = S.make_pair(H, W, L, planes=3, noise_sigma=2.0, seed=5)
+    a = dm.StereoLR(H, W, L)
+    b = dm.StereoLR(H, W, L, dm.default_params(cost_bytes=2))
+    ua, oka, ura = a.solve(sp.left, sp.right, 3, 20, 1.0)
+    ub, okb, urb = b.solve(sp.left, sp.right, 3, 20, 1.0)
+    a.sync()
+    b.sync()
+    assert np.array_equal(_np(oka), _np(okb))
+    assert np.array_equal(_np(ua), _np(ub)) and np.array_equal(_np(ura), _np(urb))

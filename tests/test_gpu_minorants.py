@@ -127,3 +127,18 @@ def test_full_frame_sampled_chains(dm, kind):
     for x in (0, 640, 1241):
         V = np.stack([O.penalty_table(int(wv[y, x]), L) for y in range(H - 1)])
         assert np.array_equal(lv[:, x] + lh[:, x], fn(lh[:, x], V)), x
+
+
+@pytest.mark.parametrize("kind", ["naive", "iterative"])
+def test_uint16_cost_storage(dm, kind):
+    """The alternatives read uint16 cost volumes too: the same numbers as uint8."""
+    H, W, L = 11, 23, 40
+    sp = S.make_pair(H, W, L, planes=3, noise_sigma=2.0, seed=77)
+    ctx = dm.Context(H, W, L, dm.default_params(cost_bytes=2))
+    ctx.cost_volume(sp.left, sp.right)
+    ctx.set_minorant(kind)
+    lb = ctx.discrete(3, lower_bounds=True)
+    cost = O.cost_volume(sp.left, sp.right, L)
+    wh, wv = O.edge_weights(sp.left)
+    rl, rlb, _, _ = O.dmm(cost, wh, wv, 3, minorant=kind)
+    assert np.array_equal(dm.labels_u16(ctx.labels()), rl) and np.array_equal(lb, rlb)
