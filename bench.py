@@ -1171,6 +1171,26 @@ def main():
         e_ms.append(a.elapsed_time(b))
     e2e_value = units * args.steps * ws / (sum(e_ms) / 1e3) / 1e6
 
+    # ---- the same frame replayed from a CUDA graph of the whole solve
+    gctx = dm.Context(H, W, L, device=str(dev), stream=torch.cuda.Stream(dev))
+    gctx.solve(d_left, d_right, NI, NP)
+    g_u = torch.empty((H, W), dtype=torch.float32, device=dev)
+    gctx.capture(d_left, d_right, NI, NP, g_u)
+    gctx.replay()
+    torch.cuda.synchronize()
+    g_ms = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(gctx.stream)
+        gctx.replay()
+        b.record(gctx.stream)
+        torch.cuda.synchronize()
+        g_ms.append(a.elapsed_time(b))
+    graph_ms = sum(g_ms) / len(g_ms)
+    gctx.sync()
+
     # ---- dominant kernel: one Dual MM pass per launch, CUDA events on the ctx stream
     avg = time_passes(ctx, d_left, d_right, NI, max(1, args.steps // 2), flush, stream)
     roofline = roofline_line(ctx, avg, H * W, L, 1, KERNEL_NAMES)
@@ -1206,6 +1226,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 2 * H * W,
                     "d2h_bytes_per_step": 4 * H * W},
+            "graph_replay_ms_per_step": round(graph_ms, 4),
             "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

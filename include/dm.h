@@ -184,6 +184,18 @@ DM_API int dm_refine(dm_ctx* ctx, int iters, const float* d_u0);
 DM_API int dm_solve(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int dmm_iters,
                     int pd_iters, float* d_u);
 
+/* Record dm_solve(ctx, d_left, d_right, dmm_iters, pd_iters, d_u) as a CUDA
+ * graph of the context's stream (which must be a stream created by the
+ * caller: the legacy stream cannot be captured, DM_ERR_STATE).  Nothing runs
+ * during the capture.  dm_replay launches the graph on the context's stream:
+ * each replay reads the images currently in d_left, d_right and writes d_u,
+ * so the buffers must stay allocated and in place.  A new capture replaces
+ * the previous one; dm_destroy releases it.  The context's state (labels,
+ * duals, disparity) after a replay is that of the solve. */
+DM_API int dm_capture(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int dmm_iters,
+                      int pd_iters, float* d_u);
+DM_API int dm_replay(dm_ctx* ctx);
+
 /* dm_solve for the next frame of a sequence: dm_cost_volume_warm, then the
  * same iterations (the refinement starts from the new labels). */
 DM_API int dm_solve_next(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right,

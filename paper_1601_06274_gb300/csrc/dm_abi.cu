@@ -532,6 +532,8 @@ DM_API int dm_destroy(dm_ctx* ctx)
     if (ctx != nullptr) {
         if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
         if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+        if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+        if (ctx->graph) cudaGraphDestroy(ctx->graph);
     }
     delete ctx;
     return DM_OK;
@@ -1199,6 +1201,42 @@ DM_API int dm_solve(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, 
     if ((rc = dm_discrete(ctx, dmm_iters, nullptr))) return rc;
     if ((rc = dm_refine(ctx, pd_iters, nullptr))) return rc;
     if (d_u != nullptr && (rc = dm_get_disparity(ctx, d_u))) return rc;
+    return DM_OK;
+}
+
+DM_API int dm_capture(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, int dmm_iters,
+                      int pd_iters, float* d_u)
+{
+    const Range range("dm_capture");
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (ctx->stream == nullptr) return DM_ERR_STATE;   // the legacy stream cannot be captured
+    if (d_left == nullptr || d_right == nullptr || d_u == nullptr || dmm_iters < 1 ||
+        pd_iters < 0)
+        return DM_ERR_ARG;
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->graph_exec = nullptr;
+    ctx->graph = nullptr;
+    DM_CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    rc = dm_solve(ctx, d_left, d_right, dmm_iters, pd_iters, d_u);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (rc != DM_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return rc != DM_OK ? rc : DM_ERR_CUDA;
+    }
+    ctx->graph = g;
+    DM_CK(cudaGraphInstantiate(&ctx->graph_exec, g, 0));
+    return DM_OK;
+}
+
+DM_API int dm_replay(dm_ctx* ctx)
+{
+    int rc = ready(ctx);
+    if (rc) return rc;
+    if (ctx->graph_exec == nullptr) return DM_ERR_STATE;
+    DM_CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
     return DM_OK;
 }
 

@@ -54,6 +54,9 @@ struct dm_ctx {
     // dm_flow_cost_volumes on the first layer (its census holds both images)
     dm_ctx* flow_partner = nullptr;
     int flow_lo1 = 0, flow_lo2 = 0;
+    // a captured solve (dm_capture) and its executable graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
 };
 
 namespace dm {

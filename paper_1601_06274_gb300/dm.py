@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
             "dm_solve_next": [_vp, _vp, _vp, _i, _i, _vp],
             "dm_cost_volume_mirrored": [_vp, _vp, _vp],
             "dm_set_minorant": [_vp, _i, _i, _i, _i],
+            "dm_capture": [_vp, _vp, _vp, _i, _i, _vp],
+            "dm_replay": [_vp],
             "dm_flow_cost_volumes": [_vp, _vp, _vp, _vp, _i, _i],
             "dm_flow_refine_bytes": [_i, _i, ctypes.POINTER(ctypes.c_size_t)],
             "dm_flow_refine": [_vp, _vp, _i, _vp, ctypes.c_size_t, _vp, _vp],
@@ -285,6 +287,22 @@ class Context:
                            pd_iters, out.data_ptr()), "dm_solve")
         self._join()
         return out
+
+    def capture(self, left, right, dmm_iters: int, pd_iters: int, out):
+        """Record a solve on these device tensors (which stay alive and in place)
+        as a CUDA graph of the context's stream (create the context with its own
+        stream)."""
+        self._graph_keep = (left, right, out)
+        self._torch.cuda.synchronize(self.device)
+        _ck(lib().dm_capture(self._h, left.data_ptr(), right.data_ptr(), int(dmm_iters),
+                             int(pd_iters), out.data_ptr()), "dm_capture")
+
+    def replay(self):
+        """Launch the captured solve after the work queued on torch's stream (new
+        images copied into the captured buffers); torch's stream then waits for it."""
+        self._fork()
+        _ck(lib().dm_replay(self._h), "dm_replay")
+        self._join()
 
     def solve_host(self, left, right, dmm_iters: int, pd_iters: int, u_out=None, labels_out=None):
         """Host buffers in and out (pinned torch CPU tensors or numpy arrays)."""

@@ -250,3 +250,15 @@ def test_batch_discrete_pass_needs_a_solve(lib):
     assert lib.dm_batch_discrete_pass(b, 2) == dm.DM_ERR_ARG
     assert lib.dm_batch_discrete_pass(None, 0) == dm.DM_ERR_ARG
     lib.dm_batch_destroy(b)
+
+
+def test_capture_and_replay_check_state_without_gpu(lib):
+    from paper_1601_06274_gb300 import dm
+    p = dm.default_params()
+    h = ctypes.c_void_p()
+    assert lib.dm_create(8, 8, 16, ctypes.byref(p), ctypes.byref(h)) == 0
+    fake = ctypes.c_void_p(4096)
+    assert lib.dm_capture(h, fake, fake, 2, 2, fake) == dm.DM_ERR_STATE
+    assert lib.dm_replay(h) == dm.DM_ERR_STATE
+    assert lib.dm_replay(None) == dm.DM_ERR_ARG
+    lib.dm_destroy(h)
