@@ -857,7 +857,7 @@ __device__ __forceinline__ void chain16(const Dmm16Args& A, int chain, uint8_t* 
 // pass writes) is staged while the previous pass drains; everything else waits
 // for that grid (griddepcontrol.wait).  Without the attribute both are no-ops.
 template <int NP, int R, bool PAD, typename DT>
-__global__ void __launch_bounds__(kWarps * 32, 3) dmm16_kernel(const Dmm16Args A)
+__global__ void __launch_bounds__(kWarps * 32, NP == 4 ? 2 : 3) dmm16_kernel(const Dmm16Args A)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t* s_taps = reinterpret_cast<uint32_t*>(smem);
