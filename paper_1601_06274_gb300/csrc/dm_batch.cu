@@ -262,7 +262,9 @@ int batch_pass(dm_batch* b, const Group& g, int which, int t, bool last)
         a.tasks = reinterpret_cast<const int2*>(b->ws + b->off_tasks) + u.begin;
         a.n_tasks = u.count;
         a.counter = counter;
-        a.grid = std::min(b->sms * b->dmm_occ, u.count);
+        // persistent CTAs: 256 labels (NP = 4) fit two per SM, the others three
+        const int occ = q.np == 4 ? std::min(b->dmm_occ, 2) : b->dmm_occ;
+        a.grid = std::min(b->sms * occ, u.count);
         a.n_desc = (int)u.pairs.size();
         for (int j = 0; j < a.n_desc; ++j) {
             dm::Dmm16Args d = b->d16[which * b->n + u.pairs[j]];

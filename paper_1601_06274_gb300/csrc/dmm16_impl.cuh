@@ -871,7 +871,7 @@ __global__ void __launch_bounds__(kWarps * 32, NP == 4 ? 2 : 3) dmm16_kernel(con
 // takes (pair, chain) tasks from a work counter, longest chains first, until
 // none are left.  All pairs share the penalty (one taps table).
 template <int NP, int R, bool PAD, typename DT>
-__global__ void __launch_bounds__(kWarps * 32, 3)
+__global__ void __launch_bounds__(kWarps * 32, NP == 4 ? 2 : 3)
     dmm16_batch_kernel(const __grid_constant__ Batch16Args B)
 {
     extern __shared__ __align__(16) uint8_t smem[];

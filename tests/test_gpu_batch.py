@@ -92,6 +92,17 @@ def test_batch_discrete_pass_continues_every_pair(dm):
         assert np.array_equal(lh.cpu().numpy().astype(np.int64), ref), k
 
 
+def test_batch_with_256_labels(dm):
+    """Pairs with 256 labels (the kernel class that runs two CTAs per SM) mixed
+    with others, against the oracle."""
+    shapes = [(8, 40, 256), (12, 30, 256), (10, 20, 128), (6, 50, 64)]
+    pairs = _pairs(shapes, 700)
+    b = dm.Batch(shapes)
+    outs = b.solve([p.left for p in pairs], [p.right for p in pairs], 3, 20)
+    b.sync()
+    _check_against_oracle(dm, b, pairs, shapes, outs, 3, 20)
+
+
 def test_batch_graph_replays_new_inputs(dm):
     import torch
     shapes = SMALL[:6]
