@@ -97,6 +97,19 @@ def test_dmm_passes_bit_exact(dm, H, W, L, path):
     _check_passes(dm, ctx, cost, wh, wv, 3, O.Params())
 
 
+@pytest.mark.parametrize("H,W,L", [(500, 16, 64), (16, 520, 48)])
+def test_dmm_passes_with_more_chains_than_one_round(dm, H, W, L):
+    """64 labels with 500 (then 520) chains in one pass: more chains than the
+    GPU holds at three CTAs per SM, so the pass runs in two rounds."""
+    left, right = _pair(H, W, L, seed=H + W)
+    ctx = _ctx(dm, H, W, L)
+    ctx.cost_volume(left, right)
+    assert ctx.path()[0] == 16
+    cost = O.cost_volume(left, right, L)
+    wh, wv = O.edge_weights(left)
+    _check_passes(dm, ctx, cost, wh, wv, 2, O.Params())
+
+
 @pytest.mark.parametrize("H,W,L", [(9, 14, 16), (5, 40, 64), (12, 8, 128), (3, 5, 200)])
 @pytest.mark.parametrize("path", [0, 1])
 def test_dmm_passes_extreme_costs_and_weights(dm, H, W, L, path):
