@@ -633,6 +633,52 @@ int or_dmm(int H, int W, int L, const int32_t* cost, const int32_t* wh, const in
                        nthreads, 0, 1, 1, 1);
 }
 
+/* The modular majorant of Primal_MM exact at `labels` (reading R39): half 0
+ * majorises f (the data cost and the horizontal edges), half 1 majorises g
+ * (the vertical edges).  bar[p][l] = (data cost if half 0) + sum over the
+ * family's edges at p of f_e(labels)/2 + cap_e [l != labels_p], cap_e =
+ * max_d omega_e r(d); then sum_p bar[p][x_p] >= the family's energy at x with
+ * equality at x = labels. */
+static void pmm_majorant(int H, int W, int L, const int32_t* cost, const int32_t* wh,
+                         const int32_t* wv, const or_tables* T, int half, const uint16_t* labels,
+                         double* bar)
+{
+    for (int y = 0; y < H; ++y)
+        for (int xx = 0; xx < W; ++xx) {
+            i64 p = (i64)y * W + xx;
+            for (int l = 0; l < L; ++l) bar[p * L + l] = half == 0 ? (double)cost[p * L + l] : 0.0;
+        }
+    for (int y = 0; y < H; ++y)
+        for (int xx = 0; xx < W; ++xx) {
+            i64 p = (i64)y * W + xx;
+            int has = half == 0 ? xx + 1 < W : y + 1 < H;
+            if (!has) continue;
+            i64 q = half == 0 ? p + 1 : p + W;
+            int om = half == 0 ? wh[p] : wv[p];
+            const i64* tab = find_table(T, om);
+            double cap = 0.0;
+            for (int d = 0; d < L; ++d) if ((double)tab[d] > cap) cap = (double)tab[d];
+            int a = labels[p], b = labels[q];
+            double cur = (double)tab[a > b ? a - b : b - a];
+            for (int l = 0; l < L; ++l) {
+                bar[p * L + l] += 0.5 * cur + (l != a ? cap : 0.0);
+                bar[q * L + l] += 0.5 * cur + (l != b ? cap : 0.0);
+            }
+        }
+}
+
+/* The majorant alone (for its pin): bar [H][W][L] of the family `half` at labels. */
+int or_pmm_majorant(int H, int W, int L, const int32_t* cost, const int32_t* wh, const int32_t* wv,
+                    double eps, double delta, double C, int half, const uint16_t* labels, double* bar)
+{
+    if (H <= 0 || W <= 0 || L <= 0 || (half != 0 && half != 1)) return OR_ERR_ARG;
+    or_tables T;
+    int rc = build_tables(&T, L, half == 0 ? wh : wv, H * W, eps, delta, C);
+    if (!rc) pmm_majorant(H, W, L, cost, wh, wv, &T, half, labels, bar);
+    free_tables(&T);
+    return rc;
+}
+
 /* Primal_MM (Alg. Primal_MM) on the grid split into horizontal chains f (data
  * and horizontal edges) and vertical chains g.  The modular majorant of a chain
  * exact at the current labelling xk (reading R39): every edge (i, j) charges
@@ -663,31 +709,7 @@ int or_primal_mm(int H, int W, int L, const int32_t* cost, const int32_t* wh, co
         for (int half = 0; half < 2; ++half) {
             /* half 0: majorise f (horizontal edges + data), minimise columns of g + f_bar;
              * half 1: majorise g (vertical edges), minimise rows of f + g_bar */
-            for (int y = 0; y < H; ++y)
-                for (int xx = 0; xx < W; ++xx) {
-                    i64 p = (i64)y * W + xx;
-                    for (int l = 0; l < L; ++l) {
-                        double v = half == 0 ? (double)cost[p * L + l] : 0.0;
-                        bar[p * L + l] = v;
-                    }
-                }
-            for (int y = 0; y < H; ++y)
-                for (int xx = 0; xx < W; ++xx) {
-                    i64 p = (i64)y * W + xx;
-                    int has = half == 0 ? xx + 1 < W : y + 1 < H;
-                    if (!has) continue;
-                    i64 q = half == 0 ? p + 1 : p + W;
-                    int om = half == 0 ? wh[p] : wv[p];
-                    const i64* tab = find_table(half == 0 ? &Th : &Tv, om);
-                    double cap = (double)tab[L - 1 < 0 ? 0 : L - 1];
-                    for (int d = 0; d < L; ++d) if ((double)tab[d] > cap) cap = (double)tab[d];
-                    int a = labels[p], b = labels[q];
-                    double cur = (double)tab[a > b ? a - b : b - a];
-                    for (int l = 0; l < L; ++l) {
-                        bar[p * L + l] += 0.5 * cur + (l != a ? cap : 0.0);
-                        bar[q * L + l] += 0.5 * cur + (l != b ? cap : 0.0);
-                    }
-                }
+            pmm_majorant(H, W, L, cost, wh, wv, half == 0 ? &Th : &Tv, half, labels, bar);
             /* minimise the other family of chains plus the modular majorant */
             int nch = half == 0 ? W : H, len = half == 0 ? H : W;
             for (int c = 0; c < nch; ++c) {

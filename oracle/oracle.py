@@ -58,79 +58,87 @@ def build(force: bool = False) -> str:
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        L = _lib
-        L.or_census.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int, u32p]
-        L.or_cost_volume.argtypes = [ctypes.c_int] * 3 + [u32p, u32p, ctypes.c_int, i32p]
-        G = ctypes.POINTER(FlowGeo)
-        L.or_flow_cost_projected.argtypes = [G, i32p, i32p]
-        L.or_flow_D.argtypes = [G, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
-        L.or_flow_D.restype = ctypes.c_double
-        L.or_flow_fit_samples.argtypes = [f64p, ctypes.c_double, f64p, f64p]
-        L.or_psd2.argtypes = [f64p]
-        L.or_flow_linearise_px.argtypes = [G, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 \
-            + [f64p, f64p, f64p]
-        L.or_flow_prox.argtypes = [ctypes.c_double] * 4 + [f64p, f64p, f64p, ctypes.c_double,
-                                                           f64p, f64p]
-        L.or_flow_energy.argtypes = [G, ctypes.c_double, f64p, f64p, ctypes.POINTER(ContParams),
-                                     f64p, f64p]
-        L.or_flow_energy.restype = ctypes.c_double
-        L.or_flow_refine.argtypes = [G, ctypes.c_double, f64p, f64p, ctypes.c_int,
-                                     ctypes.POINTER(ContParams), f64p, f64p, f64p, ctypes.c_int,
-                                     f64p]
-        L.or_cost_volume_right.argtypes = [ctypes.c_int] * 3 + [u32p, u32p, ctypes.c_int, i32p]
-        L.or_lr_check.argtypes = [ctypes.c_int, ctypes.c_int, f32p, f32p, ctypes.c_float, u8p,
-                                  f32p]
-        L.or_edge_weights.argtypes = [ctypes.c_int, ctypes.c_int, u8p] + [ctypes.c_int] * 3 + [i32p, i32p]
-        L.or_r.argtypes = [ctypes.c_double] * 4
-        L.or_r.restype = ctypes.c_double
-        L.or_r_ab.argtypes = [ctypes.c_double] * 3
-        L.or_r_ab.restype = ctypes.c_double
-        L.or_penalty_table.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                       ctypes.c_double, ctypes.c_int, i64p]
-        L.or_msg.argtypes = [ctypes.c_int, i64p, i64p, i64p]
-        L.or_min_marginals.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
-        L.or_hier_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
-        L.or_naive_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
-        L.or_iterative_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p] + \
-            [ctypes.c_int] * 3 + [i64p]
-        L.or_uniform_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, ctypes.c_double,
-                                          ctypes.c_int, f64p]
-        L.or_primal_mm.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
-                                   + [ctypes.c_int, u16p, i64p])
-        L.or_dmm_pass_kind.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p]
-                                       + [ctypes.c_double] * 3 + [ctypes.c_int, i64p, i64p]
-                                       + [ctypes.c_int] * 5)
-        L.or_dmm_kind.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
-                                  + [ctypes.c_int, i64p, i64p, i64p, u16p] + [ctypes.c_int] * 5)
-        L.or_dmm_pass.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
-                                  + [ctypes.c_int, i64p, i64p, ctypes.c_int])
-        L.or_dmm_outputs.argtypes = [ctypes.c_int] * 3 + [i64p, i64p, u16p]
-        L.or_dmm_outputs.restype = ctypes.c_int64
-        L.or_dmm.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
-                             + [ctypes.c_int, i64p, i64p, i64p, u16p, ctypes.c_int])
-        L.or_discrete_energy.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p]
-                                         + [ctypes.c_double] * 3 + [u16p])
-        L.or_discrete_energy.restype = ctypes.c_int64
-        L.or_interp.argtypes = [ctypes.c_int, f64p, ctypes.c_double]
-        L.or_interp.restype = ctypes.c_double
-        L.or_linearise_px.argtypes = [ctypes.c_int, f64p] + [ctypes.c_double] * 3 + [f64p] * 4
-        L.or_prox_data.argtypes = [ctypes.c_double] * 7
-        L.or_prox_data.restype = ctypes.c_double
-        L.or_prox_conj.argtypes = [ctypes.c_double] * 5
-        L.or_prox_conj.restype = ctypes.c_double
-        L.or_conj.argtypes = [ctypes.c_double] * 4
-        L.or_conj.restype = ctypes.c_double
-        L.or_cont_energy.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4
-                                     + [ctypes.POINTER(ContParams), f64p])
-        L.or_cont_energy.restype = ctypes.c_double
-        L.or_refine.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4 + [ctypes.c_int,
-                                ctypes.POINTER(ContParams)] + [f64p] * 5 + [ctypes.c_int, f64p])
-        L.or_convex_gap.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4
-                                    + [ctypes.POINTER(ContParams)] + [f64p] * 4 + [f64p, f64p])
-        L.or_refine_grad.argtypes = ([ctypes.c_int] * 3 + [f64p] * 5 + [ctypes.c_int,
-                                     ctypes.POINTER(ContParams)] + [f64p] * 7)
+        _lib = load(build())
     return _lib
+
+
+def load(path: str):
+    """Open a build of dm_oracle.c at `path` with every signature declared (the
+    tests also load copies with planted mistakes this way)."""
+    L = ctypes.CDLL(path)
+    L.or_census.argtypes = [ctypes.c_int, ctypes.c_int, u8p, ctypes.c_int, u32p]
+    L.or_cost_volume.argtypes = [ctypes.c_int] * 3 + [u32p, u32p, ctypes.c_int, i32p]
+    G = ctypes.POINTER(FlowGeo)
+    L.or_flow_cost_projected.argtypes = [G, i32p, i32p]
+    L.or_flow_D.argtypes = [G, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    L.or_flow_D.restype = ctypes.c_double
+    L.or_flow_fit_samples.argtypes = [f64p, ctypes.c_double, f64p, f64p]
+    L.or_psd2.argtypes = [f64p]
+    L.or_flow_linearise_px.argtypes = [G, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 \
+        + [f64p, f64p, f64p]
+    L.or_flow_prox.argtypes = [ctypes.c_double] * 4 + [f64p, f64p, f64p, ctypes.c_double,
+                                                       f64p, f64p]
+    L.or_flow_energy.argtypes = [G, ctypes.c_double, f64p, f64p, ctypes.POINTER(ContParams),
+                                 f64p, f64p]
+    L.or_flow_energy.restype = ctypes.c_double
+    L.or_flow_refine.argtypes = [G, ctypes.c_double, f64p, f64p, ctypes.c_int,
+                                 ctypes.POINTER(ContParams), f64p, f64p, f64p, ctypes.c_int,
+                                 f64p]
+    L.or_cost_volume_right.argtypes = [ctypes.c_int] * 3 + [u32p, u32p, ctypes.c_int, i32p]
+    L.or_lr_check.argtypes = [ctypes.c_int, ctypes.c_int, f32p, f32p, ctypes.c_float, u8p,
+                              f32p]
+    L.or_edge_weights.argtypes = [ctypes.c_int, ctypes.c_int, u8p] + [ctypes.c_int] * 3 + [i32p, i32p]
+    L.or_r.argtypes = [ctypes.c_double] * 4
+    L.or_r.restype = ctypes.c_double
+    L.or_r_ab.argtypes = [ctypes.c_double] * 3
+    L.or_r_ab.restype = ctypes.c_double
+    L.or_penalty_table.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int, i64p]
+    L.or_msg.argtypes = [ctypes.c_int, i64p, i64p, i64p]
+    L.or_min_marginals.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
+    L.or_hier_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
+    L.or_naive_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, i64p]
+    L.or_iterative_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p] + \
+        [ctypes.c_int] * 3 + [i64p]
+    L.or_uniform_minorant.argtypes = [ctypes.c_int, ctypes.c_int, i64p, i64p, ctypes.c_double,
+                                      ctypes.c_int, f64p]
+    L.or_pmm_majorant.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
+                                  + [ctypes.c_int, u16p, f64p])
+    L.or_primal_mm.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
+                               + [ctypes.c_int, u16p, i64p])
+    L.or_dmm_pass_kind.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p]
+                                   + [ctypes.c_double] * 3 + [ctypes.c_int, i64p, i64p]
+                                   + [ctypes.c_int] * 5)
+    L.or_dmm_kind.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
+                              + [ctypes.c_int, i64p, i64p, i64p, u16p] + [ctypes.c_int] * 5)
+    L.or_dmm_pass.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
+                              + [ctypes.c_int, i64p, i64p, ctypes.c_int])
+    L.or_dmm_outputs.argtypes = [ctypes.c_int] * 3 + [i64p, i64p, u16p]
+    L.or_dmm_outputs.restype = ctypes.c_int64
+    L.or_dmm.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p] + [ctypes.c_double] * 3
+                         + [ctypes.c_int, i64p, i64p, i64p, u16p, ctypes.c_int])
+    L.or_discrete_energy.argtypes = ([ctypes.c_int] * 3 + [i32p, i32p, i32p]
+                                     + [ctypes.c_double] * 3 + [u16p])
+    L.or_discrete_energy.restype = ctypes.c_int64
+    L.or_interp.argtypes = [ctypes.c_int, f64p, ctypes.c_double]
+    L.or_interp.restype = ctypes.c_double
+    L.or_linearise_px.argtypes = [ctypes.c_int, f64p] + [ctypes.c_double] * 3 + [f64p] * 4
+    L.or_prox_data.argtypes = [ctypes.c_double] * 7
+    L.or_prox_data.restype = ctypes.c_double
+    L.or_prox_conj.argtypes = [ctypes.c_double] * 5
+    L.or_prox_conj.restype = ctypes.c_double
+    L.or_conj.argtypes = [ctypes.c_double] * 4
+    L.or_conj.restype = ctypes.c_double
+    L.or_cont_energy.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4
+                                 + [ctypes.POINTER(ContParams), f64p])
+    L.or_cont_energy.restype = ctypes.c_double
+    L.or_refine.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4 + [ctypes.c_int,
+                            ctypes.POINTER(ContParams)] + [f64p] * 5 + [ctypes.c_int, f64p])
+    L.or_convex_gap.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4
+                                + [ctypes.POINTER(ContParams)] + [f64p] * 4 + [f64p, f64p])
+    L.or_refine_grad.argtypes = ([ctypes.c_int] * 3 + [f64p] * 5 + [ctypes.c_int,
+                                 ctypes.POINTER(ContParams)] + [f64p] * 7)
+    return L
 
 
 def _p(a: np.ndarray, t):
@@ -311,6 +319,19 @@ def primal_mm(cost, wh, wv, iters: int, labels0, P: Params = Params()):
                             _p(np.ascontiguousarray(wv, np.int32), i32p), P.eps, P.delta, P.C,
                             int(iters), _p(labels, u16p), _p(en, i64p)), "primal_mm")
     return labels, en[:iters]
+
+
+def pmm_majorant(cost, wh, wv, half: int, labels, P: Params = Params()):
+    """The modular majorant of Primal_MM exact at `labels` for the family `half`
+    (0: data + horizontal edges, 1: vertical edges), float64 [H, W, L]."""
+    cost = np.ascontiguousarray(cost, dtype=np.int32)
+    H, W, L = cost.shape
+    lab = np.ascontiguousarray(labels, dtype=np.uint16)
+    bar = np.zeros((H, W, L), dtype=np.float64)
+    _chk(lib().or_pmm_majorant(H, W, L, _p(cost, i32p), _p(np.ascontiguousarray(wh, np.int32), i32p),
+                               _p(np.ascontiguousarray(wv, np.int32), i32p), P.eps, P.delta, P.C,
+                               int(half), _p(lab, u16p), _p(bar, f64p)), "pmm_majorant")
+    return bar
 
 
 MINORANTS = {"hier": 0, "naive": 1, "iterative": 2}

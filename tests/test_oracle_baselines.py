@@ -76,6 +76,38 @@ def _tables(K):
     return table_of
 
 
+def test_primal_mm_majorant_is_above_and_exact():
+    """For each family of chains the modular majorant is >= the family's energy
+    at every labelling (enumeration) and equal at the labelling it is built at."""
+    import itertools
+    rng = np.random.default_rng(41)
+    for trial in range(6):
+        H, W, K = [(2, 3, 3), (3, 2, 3), (2, 2, 4)][trial % 3]
+        cost, wh, wv = _grid(rng, H, W, K)
+        at = rng.integers(0, K, size=(H, W)).astype(np.uint16)
+        tab = _tables(K)
+        for half in (0, 1):
+            bar = O.pmm_majorant(cost, wh, wv, half, at)
+
+            def family(lab):
+                e = 0
+                for y in range(H):
+                    for x in range(W):
+                        if half == 0:
+                            e += int(cost[y, x, lab[y][x]])
+                            if x + 1 < W:
+                                e += tab(int(wh[y, x]))[abs(lab[y][x] - lab[y][x + 1])]
+                        elif y + 1 < H:
+                            e += tab(int(wv[y, x]))[abs(lab[y][x] - lab[y + 1][x])]
+                return e
+            for flat in itertools.product(range(K), repeat=H * W):
+                lab = [flat[y * W:(y + 1) * W] for y in range(H)]
+                m = sum(bar[y, x, lab[y][x]] for y in range(H) for x in range(W))
+                assert m >= family(lab) - 1e-9
+            m0 = sum(bar[y, x, at[y, x]] for y in range(H) for x in range(W))
+            assert abs(m0 - family(at.tolist())) < 1e-9
+
+
 def test_primal_mm_is_monotone_and_above_the_minimum():
     rng = np.random.default_rng(31)
     for trial in range(8):
