@@ -496,6 +496,18 @@ def run_stream(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     avg = time_passes(ctx, *d_frames[1], NI, 1, flush, stream, warm_prev=d_frames[0])
     roof = roofline_line(ctx, avg, H * W, L, 2, KERNEL_NAMES)
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle on the first row of frame 0 (cold start), the whole path
+        from oracle import oracle as O
+        t0 = time.perf_counter()
+        O.solve(frames[0].left[:1].copy(), frames[0].right[:1].copy(), L, NI, NP,
+                nthreads=os.cpu_count())
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": round(1.0 / H / t_cpu, 6), "unit": "frames/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"row 0 of frame 0 ({W}x1x{L}), {NI} Dual MM + {NP} PD iterations, "
+                         f"{t_cpu:.2f} s; frames/s = 1 / ({H} x that time)"}
     line = {
         "metric": "frames/s (discrete+continuous), 60 warm-started frames of 1920×1080×256",
         "value": round(fps, 3), "unit": "frames/s", "n_gpus": 1, "steps": NF,
@@ -512,7 +524,7 @@ def run_stream(args):
         "lower_bound_frame1": {"warm": int(lb_warm[-1]), "cold": int(lb_cold[-1]),
                                "warm_first_iter": int(lb_warm[0]),
                                "cold_first_iter": int(lb_cold[0])},
-        "roofline": roof, "cpu_baseline": None,
+        "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_fps, 3), "unit": "frames/s", "h2d_bytes_per_step": 2 * H * W,
                 "d2h_bytes_per_step": 4 * H * W},
         "gpu_launches": launches, "clocks": clocks,
@@ -632,6 +644,20 @@ def run_batch(args):
                           + " pass over all pairs", "peak_source": src,
                 "bytes_per_launch": pass_bytes[dom],
                 "pass_ms": {"horizontal": round(pass_ms[0], 4), "vertical": round(pass_ms[1], 4)}}
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle on the first 24 rows of the batch's first pair
+        from oracle import oracle as O
+        sp0, (H0, W0, L0) = pairs[0], shapes[0]
+        rows = min(24, H0)
+        t0 = time.perf_counter()
+        O.solve(sp0.left[:rows].copy(), sp0.right[:rows].copy(), L0, NI, NP,
+                nthreads=os.cpu_count())
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": round(rows * W0 * L0 / t_cpu / 1e6, 4), "unit": "Mpixel·labels/s",
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"rows 0-{rows - 1} of pair 0 ({W0}x{rows}x{L0}), {NI} Dual MM + "
+                         f"{NP} PD iterations, {t_cpu:.2f} s"}
     line = {
         "metric": "Mpixel·labels/s (discrete+continuous), 32 mixed pairs in one CUDA graph",
         "value": round(value, 3), "unit": "Mpixel·labels/s", "n_gpus": 1, "steps": args.steps,
@@ -648,7 +674,7 @@ def run_batch(args):
                    "tune_seconds": round(tune_s, 2)},
         "single_pair_path_ms": round(single_ms, 4),
         "speedup_over_single_pair_path": round(single_ms / (tot_ms / args.steps), 3),
-        "roofline": roofline, "cpu_baseline": None,
+        "roofline": roofline, "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 3), "unit": "Mpixel·labels/s",
                 "h2d_bytes_per_step": sum(2 * H * W for H, W, _ in shapes),
                 "d2h_bytes_per_step": sum(4 * H * W for H, W, _ in shapes)},
