@@ -114,3 +114,27 @@ def test_full_size_flow(dm):
     # borders are wrong, most of the frame is right
     assert np.mean(np.abs(d1 - fp.gt1)[inner] < 1.0) > 0.7
     assert np.mean(np.abs(d2 - fp.gt2)[inner] < 1.0) > 0.7
+
+
+@pytest.mark.parametrize("case", [(10, 14, -1, 2, 0, 2), (8, 12, -100, 4, 50, 3)])
+def test_flow_minimal_and_out_of_image_ranges(dm, case):
+    """Two displacements per component; and ranges that leave the image, where
+    every cost is the out-of-image cost."""
+    H, W, lo1, K1, lo2, K2 = case
+    fp = S.make_flow_pair(H, W, max(lo1, -3), 2, 0, 2, objects=1, seed=3)
+    f = dm.Flow(H, W, lo1, K1, lo2, K2)
+    f.cost_volumes(fp.img1, fp.img2)
+    lb1, lb2 = f.discrete(2, lower_bounds=True)
+    d1, d2 = f.refine(10)
+    f.sync()
+    fl = O.Flow(fp.img1, fp.img2, lo1, K1, lo2, K2)
+    p1, p2 = fl.projected_costs()
+    assert np.array_equal(f.layer1.cost()[0].cpu().numpy().astype(np.int32), p1)
+    assert np.array_equal(f.layer2.cost()[0].cpu().numpy().astype(np.int32), p2)
+    wh, wv = O.edge_weights(fp.img1)
+    r1, rb1, _, _ = O.dmm(p1, wh, wv, 2)
+    r2, rb2, _, _ = O.dmm(p2, wh, wv, 2)
+    assert np.array_equal(lb1, rb1) and np.array_equal(lb2, rb2)
+    u1, u2, _, _ = fl.refine(r1.astype(np.float64), r2.astype(np.float64), wh, wv, 10)
+    assert np.abs(d1.cpu().numpy() - (lo1 + u1)).max() <= U_TOL
+    assert np.abs(d2.cpu().numpy() - (lo2 + u2)).max() <= U_TOL

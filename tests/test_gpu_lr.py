@@ -202,3 +202,15 @@ def test_solve_lr_with_uint16_costs(dm):
     b.sync()
     assert np.array_equal(_np(oka), _np(okb))
     assert np.array_equal(_np(ua), _np(ub)) and np.array_equal(_np(ura), _np(urb))
+
+
+@pytest.mark.parametrize("shape", [(1, 17, 8), (9, 1, 8), (2, 3, 4)])
+def test_solve_lr_degenerate_shapes(dm, shape):
+    H, W, L = shape
+    sp = S.make_pair(H, W, L, planes=2, noise_sigma=2.0, seed=H * W)
+    u, ok, ul, ur = dm.solve_lr(sp.left, sp.right, L, dmm_iters=2, pd_iters=10)
+    ref = O.solve_lr(sp.left, sp.right, L, 2, 10)
+    assert np.abs(_np(ul) - ref["u_left"]).max() <= U_TOL
+    assert np.abs(_np(ur) - ref["u_right"]).max() <= U_TOL
+    ok_g, out_g = O.lr_check(_np(ul), _np(ur), 1.0)
+    assert np.array_equal(_np(ok), ok_g) and np.array_equal(_np(u), out_g)

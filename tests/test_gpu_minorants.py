@@ -142,3 +142,13 @@ def test_uint16_cost_storage(dm, kind):
     wh, wv = O.edge_weights(sp.left)
     rl, rlb, _, _ = O.dmm(cost, wh, wv, 3, minorant=kind)
     assert np.array_equal(dm.labels_u16(ctx.labels()), rl) and np.array_equal(lb, rlb)
+
+
+@pytest.mark.parametrize("kind", ["naive", "iterative"])
+@pytest.mark.parametrize("shape", [(6, 9, 2), (1, 12, 3), (12, 1, 3)])
+def test_few_labels_and_single_rows(dm, kind, shape):
+    H, W, L = shape
+    ctx, cost, wh, wv = _setup(dm, H, W, L, H + W + L, kind, 3, (1, 4))
+    lb = ctx.discrete(3, lower_bounds=True)
+    rl, rlb, _, _ = O.dmm(cost, wh, wv, 3, minorant=kind)
+    assert np.array_equal(dm.labels_u16(ctx.labels()), rl) and np.array_equal(lb, rlb)
