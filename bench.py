@@ -15,6 +15,7 @@ solves its own frame (replicas; weak scaling; no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -335,15 +336,38 @@ def run_diff(args):
 
 
 # ---------------------------------------------------------------------------
-# Algorithmic bytes of one Dual MM pass per pixel-label (the dominant kernel)
+# Algorithmic bytes (the hot-path table's compulsory bytes, int16 duals) and
+# the bytes of the implementation's own storage
 # ---------------------------------------------------------------------------
 
+def survey_pass_bytes(HW: int, L: int) -> dict:
+    """Compulsory bytes of one Dual MM pass with int16 duals: the horizontal
+    pass reads c (1 B) and lambda_v (2 B) and writes lambda_h (2 B) per
+    pixel-label; the vertical pass reads lambda_h and writes lambda_v (2 + 2 B)."""
+    return {0: HW * L * 5, 1: HW * L * 4}
+
+
+def survey_frame_bytes(HW: int, L: int, cost_bytes: int, dmm_iters: int, pd_iters: int,
+                       warps: int) -> int:
+    """Compulsory bytes of one frame: census + cost (2 B/px read, L cost_bytes
+    B/px written), Dual MM at 9 B per pixel-label and iteration (the first
+    iteration's lambda_v read skipped), linearisation at 23 B/px per warp and
+    60 B/px per primal-dual iteration."""
+    return (HW * (2 + L * cost_bytes) + HW * L * (9 * dmm_iters - 2) + HW * 23 * warps
+            + HW * 60 * pd_iters)
+
+
 def dmm_pass_bytes(kernel: int, delta_bytes: int, cost_bytes: int, HW: int, L: int) -> dict:
-    """Bytes a pass must move at least.  16-bit kernel: the horizontal pass reads
-    the deltas of c + lambda_v and writes those of lambda_h (plus a 4-byte base
-    per pixel each); the vertical pass reads lambda_h and c and writes c +
-    lambda_v.  int32 kernel: the horizontal pass reads c and lambda_v and writes
-    lambda_h, the vertical pass reads lambda_h and writes lambda_v."""
+    """Bytes the implementation's own storage makes a pass move at least.
+    Packed kernels (8, 16): the horizontal pass reads the deltas of c +
+    lambda_v and c and writes those of lambda_h, the vertical pass reads
+    lambda_h and c and writes c + lambda_v (the deltas plus a 4-byte base per
+    pixel each; the one-warp kernel reads c only on the vertical pass).  int32
+    kernel: the horizontal pass reads c and lambda_v and writes lambda_h, the
+    vertical pass reads lambda_h and writes lambda_v."""
+    if kernel == 8:
+        return {0: HW * ((2 * delta_bytes + cost_bytes) * L + 8),
+                1: HW * ((2 * delta_bytes + cost_bytes) * L + 8)}
     if kernel == 16:
         return {0: HW * (2 * delta_bytes * L + 8),
                 1: HW * ((2 * delta_bytes + cost_bytes) * L + 8)}
@@ -381,36 +405,60 @@ def time_passes(ctx, d_left, d_right, iters, reps, flush, stream, warm_prev=None
     return {w: sum(a.elapsed_time(b) for a, b in v) / len(v) for w, v in pass_ms.items()}
 
 
-def roofline_line(ctx, avg, HW, L, cost_bytes, kernel_names):
+def source_tag(kernel_file: str) -> str:
+    """First 12 hex digits of the SHA-256 of a kernel's source file: a profile
+    figure is used only while the kernel it was captured from is unchanged."""
+    path = os.path.join(ROOT, "paper_1601_06274_gb300", "csrc", kernel_file)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:12]
+
+
+def roofline_line(ctx, avg, HW, L, cost_bytes, kernel_names, workload="kitti"):
+    """Roofline of the slower Dual MM pass: achieved = the compulsory bytes of
+    the pass (int16 duals) / its average duration; frac_storage uses the bytes
+    of the implementation's own storage instead.  traffic and the instruction
+    count come from an ncu capture of the same kernel source, else null."""
     kernel, dbytes = ctx.path()
-    bytes_per = dmm_pass_bytes(kernel, dbytes, cost_bytes, HW, L)
+    alg = survey_pass_bytes(HW, L)
+    own = dmm_pass_bytes(kernel, dbytes, cost_bytes, HW, L)
     dom = max((0, 1), key=lambda w: avg[w])
     peak, src = hbm_peak()
-    achieved = bytes_per[dom] / (avg[dom] / 1e3) / 1e9
-    return {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
-            "kernel": kernel_names[kernel] + (" horizontal" if dom == 0 else " vertical")
-            + " pass", "peak_source": src,
-            "bytes_per_launch": bytes_per[dom],
-            "dual_storage": f"{dbytes}-byte deltas" if kernel == 16 else "int32",
+    sec = avg[dom] / 1e3
+    achieved = alg[dom] / sec / 1e9
+    name = kernel_names[kernel] + (" horizontal" if dom == 0 else " vertical") + " pass"
+    key = (workload, name, source_tag(KERNEL_FILES[kernel]))
+    line = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(key),
+            "kernel": name, "peak_source": src, "bytes_per_launch": alg[dom],
+            "bytes_rule": "5 B (horizontal) / 4 B (vertical) per pixel-label: int16 duals",
+            "frac_storage": round(own[dom] / sec / 1e9 / peak, 4),
+            "storage_bytes_per_launch": own[dom],
+            "dual_storage": f"{dbytes}-byte deltas" if kernel in (8, 16) else "int32",
             "pass_ms": {"horizontal": round(avg[0], 4), "vertical": round(avg[1], 4)}}
+    inst = NCU_INSTRUCTIONS.get(key)
+    if inst is not None:
+        rate = inst / sec / 1e9
+        line["issue_frac"] = round(rate / ISSUE_PEAK_GINST_S, 4)
+        line["issue"] = {"warp_instructions_per_launch": inst, "achieved_ginst_s": round(rate, 1),
+                         "peak_ginst_s": round(ISSUE_PEAK_GINST_S, 1)}
+    return line
 
 
-KERNEL_NAMES = {16: "dmm16_kernel", 32: "dmm_pass_kernel"}
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from the ncu capture in
-# profiles/ of the kernel as built now (keyed by workload and kernel); a kernel
-# changed since its capture has no entry and reports null
-NCU_TRAFFIC = {("kitti", "dmm16_kernel horizontal pass"): 351_220_224,
-               ("kitti", "dmm16_kernel vertical pass"): 289_238_272,
-               # dram__bytes.sum.per_second x gpu__time_duration.sum of the capture
-               ("minorants", "dmm_alt_kernel horizontal pass"): 3_585_900_000,
-               ("minorants", "dmm_alt_kernel vertical pass"): 3_333_000_000,
-               ("lr", "lr_check_kernel"): 3_732_000}
-# smsp__inst_executed.sum per launch from the same capture: the pass is bound by
-# instruction issue, so its issue rate is reported beside the HBM roofline,
-# against 152 SMs x 4 schedulers x 1 warp-instruction per cycle at 2070 MHz
-NCU_INSTRUCTIONS = {("kitti", "dmm16_kernel horizontal pass"): 431_540_250,
-                    ("kitti", "dmm16_kernel vertical pass"): 404_750_412}
+KERNEL_NAMES = {8: "dmg_kernel", 16: "dmm16_kernel", 32: "dmm_pass_kernel"}
+KERNEL_FILES = {8: "dmg_impl.cuh", 16: "dmm16_impl.cuh", 32: "dmm.cu"}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from the ncu captures
+# summarised in profiles/, keyed by workload, kernel and the kernel source's tag
+# (source_tag) at capture time: a kernel changed since its capture reports null
+NCU_TRAFFIC = {
+    # dram__bytes.sum.per_second x gpu__time_duration.sum of the capture
+    ("minorants", "dmm_alt_kernel horizontal pass", "d05e9b6ae61e"): 3_585_900_000,
+    ("minorants", "dmm_alt_kernel vertical pass", "d05e9b6ae61e"): 3_333_000_000,
+    ("lr", "lr_check_kernel", "68c80f87cd1d"): 3_732_000,
+}
+# smsp__inst_executed.sum per launch from the same captures: a Dual MM pass is
+# bound by instruction issue and latency, so its issue rate is reported beside
+# the HBM roofline, against 152 SMs x 4 schedulers x 1 warp-instruction per
+# cycle at 2070 MHz
+NCU_INSTRUCTIONS = {}
 ISSUE_PEAK_GINST_S = 152 * 4 * 2.070
 
 
@@ -805,11 +853,11 @@ def run_lr(args):
     avg = time_passes(single, d_left, d_right, NI, max(1, args.steps // 2), flush,
                       single.stream)
     roofline = roofline_line(single, avg, H * W, L, 1, KERNEL_NAMES)
-    roofline["traffic"] = NCU_TRAFFIC.get(("kitti", roofline["kernel"]))
     roofline["check_kernel"] = {"kernel": "lr_check_kernel", "us": round(chk_ms * 1e3, 2),
                                 "timing": f"{NB} launches on rotating buffers in one graph",
                                 "bytes_per_launch": LR_CHECK_BYTES * H * W,
-                                "traffic": NCU_TRAFFIC.get(("lr", "lr_check_kernel")),
+                                "traffic": NCU_TRAFFIC.get(("lr", "lr_check_kernel",
+                                                            source_tag("lr.cu"))),
                                 "achieved_gbs": round(chk_gbs, 1),
                                 "frac": round(chk_gbs / peak, 4)}
 
@@ -949,7 +997,7 @@ def run_minorants(args):
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "kernel": "dmm_alt_kernel " + ("horizontal" if dom == 0 else "vertical") + " pass",
                 "peak_source": src, "bytes_per_launch": bytes_per[dom]}
-    roofline["traffic"] = NCU_TRAFFIC.get(("minorants", roofline["kernel"]))
+    roofline["traffic"] = NCU_TRAFFIC.get(("minorants", roofline["kernel"], source_tag("dmm.cu")))
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -1240,15 +1288,10 @@ def main():
     # ---- dominant kernel: one Dual MM pass per launch, CUDA events on the ctx stream
     avg = time_passes(ctx, d_left, d_right, NI, max(1, args.steps // 2), flush, stream)
     roofline = roofline_line(ctx, avg, H * W, L, 1, KERNEL_NAMES)
-    roofline["traffic"] = NCU_TRAFFIC.get(("kitti", roofline["kernel"]))
-    inst = NCU_INSTRUCTIONS.get(("kitti", roofline["kernel"]))
-    if inst is not None:
-        dur = roofline["pass_ms"]["horizontal" if "horizontal" in roofline["kernel"] else "vertical"]
-        rate = inst / (dur / 1e3) / 1e9
-        roofline["issue"] = {"warp_instructions_per_launch": inst,
-                             "achieved_ginst_s": round(rate, 1),
-                             "peak_ginst_s": round(ISSUE_PEAK_GINST_S, 1),
-                             "frac": round(rate / ISSUE_PEAK_GINST_S, 4)}
+    peak = roofline["peak"]
+    frame_bytes = survey_frame_bytes(H * W, L, 1, NI, NP, 5)
+    roofline["frame_bytes"] = frame_bytes
+    roofline["frame_frac"] = round(frame_bytes / (tot_ms / args.steps / 1e3) / 1e9 / peak, 4)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

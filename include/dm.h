@@ -92,8 +92,11 @@ typedef struct dm_params {
     double h;               /* linearisation half-width in labels (Sec. 3.1)    */
     int32_t warps;          /* re-linearisations of the data term (Sec. 3.1)    */
     int32_t dmm_path;       /* Dual MM kernel: 0 = automatic (packed 16-bit     */
-                            /* arithmetic whenever its value bounds hold),       */
-                            /* 1 = always the int32 kernel                       */
+                            /* arithmetic on lane groups with 8-bit messages     */
+                            /* whenever its value bounds hold, else one warp     */
+                            /* per chain, else int32), 1 = always the int32      */
+                            /* kernel, 2 = packed one-warp-per-chain kernel      */
+                            /* where its bounds hold, else int32                 */
     int32_t cost_bytes;     /* storage of the cost volume: 0 or 1 = uint8,       */
                             /* 2 = uint16                                        */
     int32_t reserved[5];
@@ -496,9 +499,10 @@ DM_API int dm_flow_refine(dm_ctx* layer1, dm_ctx* layer2, int iters, void* d_scr
 #define DM_MINORANT_ITERATIVE 2
 DM_API int dm_set_minorant(dm_ctx* ctx, int kind, int max_pass, int gamma_num, int gamma_den);
 
-/* The Dual MM kernel chosen for the current cost volume: *kernel = 16 (packed
- * 16-bit arithmetic, dual deltas of *delta_bytes bytes per label) or 32 (int32
- * kernel, *delta_bytes = 4).  Host only. */
+/* The Dual MM kernel chosen for the current cost volume: *kernel = 8 (packed
+ * 16-bit arithmetic on lane groups, 8-bit messages), 16 (packed 16-bit
+ * arithmetic, one warp per chain) -- both with dual deltas of *delta_bytes
+ * bytes per label -- or 32 (int32 kernel, *delta_bytes = 4).  Host only. */
 DM_API int dm_get_path(const dm_ctx* ctx, int* kernel, int* delta_bytes);
 
 /* Number of kernels this context has enqueued since dm_create (host-side

@@ -18,6 +18,10 @@ namespace {
 
 constexpr int kMaxIters = 4096;
 constexpr int kMaxDelta16 = 255 + 2 * (8000 + 1);  // largest delta the 16-bit kernel admits
+// the lane-group kernel: deltas up to 8000 keep its padded labels (read as
+// 16383) out of every minimum, and caps up to 254 keep messages in one byte
+constexpr int kMaxDeltaG = 8000;
+constexpr int kMaxCapG = 254;
 
 #define DM_CK(call)                                  \
     do {                                             \
@@ -305,6 +309,15 @@ int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
     dm::Dmm16Args a = dm16_args(c, which);
     a.labels = labels;
     a.lb = lb;
+    if (c->use_g) {
+        // 8-bit messages [chains][n][16 gsz], then the int32 offsets
+        const size_t msg = align_up((size_t)c->H * c->W * 16 * c->gsz, 256);
+        a.fofs = reinterpret_cast<int32_t*>(c->ws + c->lay.fmsg + msg);
+        a.bofs = reinterpret_cast<int32_t*>(c->ws + c->lay.bmsg + msg);
+        DM_CK(dm::launch_dmg_pass(a, c->gsz, c->radius, c->delta_bytes, c->stream));
+        c->launches += 1;
+        return DM_OK;
+    }
     DM_CK(dm::launch_dmm16_pass(a, c->np16, c->radius, c->delta_bytes, c->stream));
     c->launches += 1;
     return DM_OK;
@@ -320,6 +333,7 @@ void set_path(dm_ctx* c, int cost_max, bool user_weights)
     c->user_weights = user_weights;
     c->cost_max = cost_max;
     c->use16 = c->can16 && c->minorant == 0 && cost_max + 2 * (p2 + 1) <= kMaxDelta16;
+    c->use_g = c->use16 && c->can_g && cost_max + 2 * (p2 + 1) <= kMaxDeltaG && p2 <= kMaxCapG;
     c->delta_bytes = (cost_max + 2 * (p2 + 1) <= 255) ? 1 : 2;
 }
 
@@ -477,8 +491,10 @@ DM_API int dm_create(int H, int W, int L, const dm_params* p, dm_ctx** out)
     }
     // the 16-bit kernel stages each unary row as four async copies of L/4 bytes
     // (uint8 deltas) or L/2 bytes (int16), so L must be a multiple of 16
-    c->can16 = c->discrete_ok && p->dmm_path == 0 && (L % 16) == 0 && c->p2_all <= 8000 &&
-               H <= 8192 && W <= 8192;
+    c->can16 = c->discrete_ok && (p->dmm_path == 0 || p->dmm_path == 2) && (L % 16) == 0 &&
+               c->p2_all <= 8000 && H <= 8192 && W <= 8192;
+    c->can_g = c->can16 && p->dmm_path == 0;
+    c->gsz = L <= 16 ? 1 : (L <= 32 ? 2 : (L <= 64 ? 4 : (L <= 128 ? 8 : 16)));
     // workspace layout
     dm::Layout& l = c->lay;
     size_t tot = 0;
@@ -1490,7 +1506,7 @@ DM_API int dm_set_minorant(dm_ctx* ctx, int kind, int max_pass, int gamma_num, i
 DM_API int dm_get_path(const dm_ctx* ctx, int* kernel, int* delta_bytes)
 {
     if (ctx == nullptr || kernel == nullptr || delta_bytes == nullptr) return DM_ERR_ARG;
-    *kernel = ctx->use16 ? 16 : 32;
+    *kernel = ctx->use16 ? (ctx->use_g ? 8 : 16) : 32;
     *delta_bytes = ctx->use16 ? ctx->delta_bytes : 4;
     return DM_OK;
 }

@@ -15,6 +15,11 @@ struct dm_ctx {
     bool can16 = false;
     bool use16 = false;
     int np16 = 1;
+    // the lane-group kernel (dmg_impl.cuh) is the packed kernel of choice when
+    // every penalty cap fits its 8-bit messages; gsz lanes of 16 labels per message
+    bool can_g = false;
+    bool use_g = false;
+    int gsz = 8;
     int delta_bytes = 2;
     int p2_all = 0;             // largest cap omega*C over every usable omega
     int p2_used = 0;            // largest cap over w_hi, w_lo

@@ -1,0 +1,6 @@
+// Dual MM kernels on groups of 2 lane(s) (up to 32 labels), uint8_t dual deltas.
+#include "dmg_impl.cuh"
+
+namespace dm {
+template cudaError_t launch_g<2, uint8_t>(const Dmm16Args&, int, cudaStream_t);
+}  // namespace dm

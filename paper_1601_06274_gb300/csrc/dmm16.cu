@@ -1,6 +1,7 @@
 // Dual MM pass with packed 16-bit arithmetic: dispatch over the label classes
-// (instantiated in dmm16_np*_*.cu from dmm16_impl.cuh) and the conversion
-// kernels between the packed dual storage and int32.
+// of the lane-group kernel (dmg_g*_*.cu from dmg_impl.cuh) and of the
+// one-warp-per-chain kernel (dmm16_np*_*.cu from dmm16_impl.cuh), and the
+// conversion kernels between the packed dual storage and int32.
 
 #include <climits>
 
@@ -12,6 +13,8 @@ template <int NP, typename DT>
 cudaError_t launch16(const Dmm16Args& a, int radius, cudaStream_t s);
 template <int NP, typename DT>
 cudaError_t launch16_batch(const Batch16Args& b, int radius, bool pad, cudaStream_t s);
+template <int G, typename DT>
+cudaError_t launch_g(const Dmm16Args& a, int radius, cudaStream_t s);
 
 namespace {
 
@@ -109,6 +112,26 @@ cudaError_t launch_dmm16_pass(const Dmm16Args& a, int np, int radius, int delta_
     if (np == 1) return launch16<1, int16_t>(a, radius, s);
     if (np == 2) return launch16<2, int16_t>(a, radius, s);
     return launch16<4, int16_t>(a, radius, s);
+}
+
+cudaError_t launch_dmg_pass(const Dmm16Args& a, int g, int radius, int delta_bytes, cudaStream_t s)
+{
+    if (delta_bytes == 1) {
+        switch (g) {
+            case 1: return launch_g<1, uint8_t>(a, radius, s);
+            case 2: return launch_g<2, uint8_t>(a, radius, s);
+            case 4: return launch_g<4, uint8_t>(a, radius, s);
+            case 8: return launch_g<8, uint8_t>(a, radius, s);
+            default: return launch_g<16, uint8_t>(a, radius, s);
+        }
+    }
+    switch (g) {
+        case 1: return launch_g<1, int16_t>(a, radius, s);
+        case 2: return launch_g<2, int16_t>(a, radius, s);
+        case 4: return launch_g<4, int16_t>(a, radius, s);
+        case 8: return launch_g<8, int16_t>(a, radius, s);
+        default: return launch_g<16, int16_t>(a, radius, s);
+    }
 }
 
 cudaError_t launch_dmm16_batch(const Batch16Args& b, int np, int radius, bool pad, int delta_bytes,

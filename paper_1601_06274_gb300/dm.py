@@ -432,7 +432,8 @@ class Context:
         return du
 
     def path(self):
-        """(Dual MM kernel: 16 or 32, bytes per dual delta)"""
+        """(Dual MM kernel: 8 lane groups, 16 one warp per chain, 32 int32;
+        bytes per dual delta)"""
         k, d = ctypes.c_int(), ctypes.c_int()
         _ck(lib().dm_get_path(self._h, ctypes.byref(k), ctypes.byref(d)), "dm_get_path")
         return k.value, d.value

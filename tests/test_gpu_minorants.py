@@ -85,7 +85,7 @@ def test_switching_minorants(dm):
     ctx.set_minorant("naive")
     naive_lb = ctx.discrete(3, lower_bounds=True)
     ctx.set_minorant("hier")
-    assert ctx.path()[0] == 16
+    assert ctx.path()[0] == 8
     lb = ctx.discrete(3, lower_bounds=True)
     assert np.array_equal(lb, ref_lb)
     assert np.array_equal(dm.labels_u16(ctx.labels()), dm.labels_u16(ref.labels()))

@@ -61,7 +61,7 @@ def _check_passes(ctx, cost, wh, wv, iters, P=O.Params()):
 
 @pytest.mark.parametrize("H,W,L", [(48, 64, 16), (17, 31, 48), (7, 19, 64), (5, 11, 128),
                                    (4, 9, 256)])
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path", [0, 1, 2])
 def test_u16_census_passes_bit_exact(dm, H, W, L, path):
     sp = S.make_pair(H, W, L, planes=3, noise_sigma=2.0, seed=3 * H + W)
     ctx = _ctx(dm, H, W, L, dmm_path=path)
@@ -115,7 +115,7 @@ def test_u16_refine_matches_oracle(dm):
 
 @pytest.mark.parametrize("H,W,L", [(48, 64, 16), (30, 70, 64)])
 @pytest.mark.parametrize("cost_bytes", [1, 2])
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path", [0, 1, 2])
 def test_warm_started_sequence_matches_oracle(dm, H, W, L, cost_bytes, path):
     """frame 0 cold, then each frame starts Dual MM from the previous lambda_v"""
     iters, pd = 3, 20
