@@ -864,10 +864,53 @@ double or_cont_energy(int H, int W, int L, const double* cost, const double* alp
  * State arrays are H*W (edge arrays store the edge at its left/top pixel; the
  * last column of *_h and last row of *_v are unused and kept at 0).
  * If init is nonzero, p and q are reset to 0 first; u holds u0 on entry.
- * energy (nullable): E(u) after each warp. */
+ * energy (nullable): E(u) after each warp.
+ * noise > 0 (or_refine_perturbed only): after every iteration each of u, p and
+ * q is multiplied by 1 + noise * U, U uniform in [-1, 1) from splitmix64. */
+static int refine_run(int H, int W, int L, const double* cost, const double* alpha, const double* wh,
+                      const double* wv, int iters, const or_cont_params* P, double* u, double* ph,
+                      double* pv, double* qh, double* qv, int init, double* energy, double noise,
+                      uint64_t seed);
+
 int or_refine(int H, int W, int L, const double* cost, const double* alpha, const double* wh,
               const double* wv, int iters, const or_cont_params* P, double* u, double* ph,
               double* pv, double* qh, double* qv, int init, double* energy)
+{
+    return refine_run(H, W, L, cost, alpha, wh, wv, iters, P, u, ph, pv, qh, qv, init, energy,
+                      0.0, 0);
+}
+
+/* splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014): the finaliser applied to seed + (n + 1) * golden
+ * gamma, i.e. the n-th output of the generator started at seed; mapped to
+ * [-1, 1) with 53 bits. */
+static double splitmix_unit(uint64_t seed, uint64_t n)
+{
+    uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+/* The refinement with relative noise of size `noise` put on the state (u, p,
+ * q) after every iteration: a model of rounding the state to a shorter float
+ * (2^-24 for float32), used to measure how far the double-precision result at
+ * each pixel is determined by a computation that carries that precision. */
+int or_refine_perturbed(int H, int W, int L, const double* cost, const double* alpha,
+                        const double* wh, const double* wv, int iters, const or_cont_params* P,
+                        double* u, double* ph, double* pv, double* qh, double* qv, int init,
+                        double noise, uint64_t seed)
+{
+    if (!(noise >= 0.0)) return OR_ERR_ARG;
+    return refine_run(H, W, L, cost, alpha, wh, wv, iters, P, u, ph, pv, qh, qv, init, NULL,
+                      noise, seed);
+}
+
+static int refine_run(int H, int W, int L, const double* cost, const double* alpha, const double* wh,
+                      const double* wv, int iters, const or_cont_params* P, double* u, double* ph,
+                      double* pv, double* qh, double* qv, int init, double* energy, double noise,
+                      uint64_t seed)
 {
     if (H <= 0 || W <= 0 || L < 2 || P->warps <= 0) return OR_ERR_ARG;
     i64 N = (i64)H * W;
@@ -884,6 +927,7 @@ int or_refine(int H, int W, int L, const double* cost, const double* alpha, cons
     const double ap = P->eps;                                /* alpha of R+ */
     const double bq = P->C + P->delta - P->eps * P->delta;   /* beta of R- (alpha = 0) */
     const double tau = P->tau, sigma = P->sigma;
+    uint64_t step = 0;   /* iterations done (the noise counter) */
     int base = iters / P->warps, extra = iters % P->warps;
     for (int w = 0; w < P->warps; ++w) {
         int nit = base + (w < extra ? 1 : 0);
@@ -924,6 +968,13 @@ int or_refine(int H, int W, int L, const double* cost, const double* alpha, cons
                     }
                 }
             memcpy(u, un, N * sizeof(double));
+            if (noise > 0.0) {
+                double* st[5] = {u, ph, pv, qh, qv};
+                for (int a = 0; a < 5; ++a)
+                    for (i64 p = 0; p < N; ++p)
+                        st[a][p] *= 1.0 + noise * splitmix_unit(seed, ((uint64_t)step * 5 + a) * N + p);
+                ++step;
+            }
         }
         if (energy) energy[w] = or_cont_energy(H, W, L, cost, alpha, wh, wv, P, u);
     }

@@ -134,6 +134,9 @@ def load(path: str):
     L.or_cont_energy.restype = ctypes.c_double
     L.or_refine.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4 + [ctypes.c_int,
                             ctypes.POINTER(ContParams)] + [f64p] * 5 + [ctypes.c_int, f64p])
+    L.or_refine_perturbed.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4 + [ctypes.c_int,
+                                      ctypes.POINTER(ContParams)] + [f64p] * 5
+                                      + [ctypes.c_int, ctypes.c_double, ctypes.c_uint64])
     L.or_convex_gap.argtypes = ([ctypes.c_int] * 3 + [f64p] * 4
                                 + [ctypes.POINTER(ContParams)] + [f64p] * 4 + [f64p, f64p])
     L.or_refine_grad.argtypes = ([ctypes.c_int] * 3 + [f64p] * 5 + [ctypes.c_int,
@@ -446,6 +449,38 @@ def refine(cost, wh, wv, u0, iters: int, P: Params = Params(), alpha=None, state
                          _p(u, f64p), _p(ph, f64p), _p(pv, f64p), _p(qh, f64p), _p(qv, f64p),
                          init, _p(energy, f64p)), "refine")
     return u, (ph, pv, qh, qv), energy
+
+
+def refine_perturbed(cost, wh, wv, u0, iters: int, noise: float, seed: int,
+                     P: Params = Params(), alpha=None):
+    """The refinement with the state (u, p, q) multiplied by 1 + noise * U
+    (U uniform in [-1, 1), splitmix64 from seed) after every iteration; noise =
+    2^-24 models keeping the state in float32.  Returns u."""
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    H, W, L = cost.shape
+    u = np.array(u0, dtype=np.float64).reshape(H, W).copy()
+    ph, pv, qh, qv = (np.zeros((H, W)) for _ in range(4))
+    al = np.ascontiguousarray(np.broadcast_to(P.alpha if alpha is None else alpha, (H, W)), np.float64)
+    cp = P.cont()
+    _chk(lib().or_refine_perturbed(H, W, L, _p(cost, f64p), _p(al, f64p),
+                                   _p(np.ascontiguousarray(wh, np.float64), f64p),
+                                   _p(np.ascontiguousarray(wv, np.float64), f64p), iters,
+                                   ctypes.byref(cp), _p(u, f64p), _p(ph, f64p), _p(pv, f64p),
+                                   _p(qh, f64p), _p(qv, f64p), 1, float(noise), int(seed)),
+         "refine_perturbed")
+    return u
+
+
+def fp32_spread(cost, wh, wv, u0, iters: int, P: Params = Params(), seeds=range(8), alpha=None):
+    """Per pixel, the largest distance between the refinement and its float32
+    noise model (refine_perturbed with noise 2^-24) over the given seeds: how
+    far the double-precision result is determined at float32 precision."""
+    u = refine(cost, wh, wv, u0, iters, P, alpha=alpha)[0]
+    spread = np.zeros_like(u)
+    for s in seeds:
+        spread = np.maximum(spread, np.abs(
+            refine_perturbed(cost, wh, wv, u0, iters, 2.0 ** -24, s, P, alpha=alpha) - u))
+    return spread
 
 
 def convex_gap(cost, wh, wv, u0, u, ph, pv, P: Params, alpha=None):

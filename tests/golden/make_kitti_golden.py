@@ -4,7 +4,13 @@ The full 1242x375x128 frame (10 Dual MM iterations, 100 primal-dual
 iterations) takes the oracle tens of minutes, too long for a test, so its
 results are stored: hashes of the inputs, the cost volume and the labels, the
 lower bound of every iteration, a sample of labels and of the refined
-disparity, and the final continuous energy.  Run:  python tests/golden/make_kitti_golden.py
+disparity, and the final continuous energy (kitti_1242x375x128.json), and, in
+kitti_1242x375x128_u.npz, the whole refined disparity rounded to float32 (the
+rounding error is below 1e-5 px) with its float32 spread: per pixel, the
+largest move of the double-precision result when the state is perturbed by
+float32-sized relative noise after every iteration (oracle.fp32_spread, eight
+seeds), stored as float16 rounded up and at least 1e-5.
+Run:  python tests/golden/make_kitti_golden.py
 """
 
 import hashlib
@@ -24,6 +30,16 @@ from paper_1601_06274_gb300 import synthetic as S  # noqa: E402
 
 def sha(a: np.ndarray) -> str:
     return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def round_up_f16(a, floor):
+    """max(a, floor) as float16, rounded up (the stored spread never
+    understates the computed one; the floor keeps the file small)"""
+    a = np.maximum(a, floor)
+    h = a.astype(np.float16)
+    low = h.astype(np.float64) < a
+    h[low] = np.nextafter(h[low], np.float16(np.inf))
+    return h
 
 
 def main():
@@ -49,9 +65,14 @@ def main():
         "energy": float(res["energy"][-1]),
         "oracle_seconds": round(time.time() - t0, 1),
     }
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "kitti_1242x375x128.json")
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "kitti_1242x375x128.json")
     with open(path, "w") as fh:
         json.dump(out, fh)
+    spread = O.fp32_spread(res["cost"].astype(np.float64), res["wh"], res["wv"],
+                           res["labels"].astype(np.float64), spec["pd_iters"])
+    np.savez_compressed(os.path.join(here, "kitti_1242x375x128_u.npz"),
+                        u=res["u"].astype(np.float32), spread=round_up_f16(spread, 1e-5))
     print("wrote", path, "in", out["oracle_seconds"], "s")
 
 

@@ -3,9 +3,20 @@
 The CPU oracle needs minutes for this frame, so its results were stored by
 tests/golden/make_kitti_golden.py (which calls only the oracle and the input
 generator): input and cost-volume hashes, the lower bound after each of the
-10 Dual MM iterations, the label hash, and 4096 sampled labels and refined
-disparities with the final energy.  The GPU runs the frame through the same
-C ABI calls as bench.py.
+10 Dual MM iterations, the label hash, 4096 sampled labels, the final energy,
+the whole refined disparity (float32) and its float32 spread.  The GPU runs the
+frame through the same C ABI calls as bench.py.
+
+The refinement's difference-of-convex iteration (Sec. 2.4) amplifies rounding
+where the concave part is active: the q step adds tau A u and the u step
+subtracts tau A^T(-q), a pair with growth factor above one until a prox
+saturates.  On this frame the double-precision result moves by up to about two
+pixels at a few hundred pixels when the state carries float32-sized relative
+noise (2^-24) after every iteration, so no float32 computation determines it
+there to 1e-3.  The check is therefore made at every pixel against the
+oracle's own spread: |u - u_oracle| <= 1e-3 + spread, where spread is the
+largest move of the oracle under that noise over eight seeds; at the pixels
+with spread <= 1e-4 (more than 99 % of them) this is the plain 1e-3 bar.
 """
 
 import hashlib
@@ -20,6 +31,7 @@ from paper_1601_06274_gb300 import synthetic as S
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "kitti_1242x375x128.json")
+GOLDEN_U = os.path.join(os.path.dirname(__file__), "golden", "kitti_1242x375x128_u.npz")
 U_TOL = 1e-3
 E_TOL = 1e-5
 
@@ -67,6 +79,16 @@ def test_full_frame_solve_matches_oracle(setup):
     e = ctx.energy()
     ref = np.array(g["sample_u"])
     assert np.abs(u[g["sample_y"], g["sample_x"]] - ref).max() <= U_TOL
+    # every pixel against the oracle's whole refined disparity, within the
+    # oracle's own float32 spread
+    z = np.load(GOLDEN_U)
+    u_ref, spread = z["u"].astype(np.float64), z["spread"].astype(np.float64)
+    assert u_ref.shape == (H, W) and spread.shape == (H, W)
+    err = np.abs(u - u_ref)
+    assert (err - spread).max() <= U_TOL
+    stable = spread <= 1e-4
+    assert stable.mean() >= 0.99
+    assert err[stable].max() <= U_TOL
     assert abs(e - g["energy"]) <= E_TOL * abs(g["energy"])
     # invariants that hold at any size: the refined disparity stays within the
     # warps' boxes around the labels and inside the label range
