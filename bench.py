@@ -405,6 +405,34 @@ def time_passes(ctx, d_left, d_right, iters, reps, flush, stream, warm_prev=None
     return {w: sum(a.elapsed_time(b) for a, b in v) / len(v) for w, v in pass_ms.items()}
 
 
+def time_stages(ctx, d_left, d_right, dmm_iters, pd_iters, flush, stream, reps=5):
+    """Average duration of each stage of one solve (CUDA events on the
+    context's stream, L2 flushed before each): the census and cost volume, the
+    dmm_iters Dual MM iterations, and the pd_iters refinement iterations."""
+    import torch
+    ev = {"census_and_cost_volume": [], "dual_mm": [], "refinement": []}
+
+    def rec(name, fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ev[name].append((a, b))
+
+    with torch.cuda.stream(stream):
+        for r in range(reps):
+            flush.fill_(r & 0xff)
+            rec("census_and_cost_volume", lambda: ctx.cost_volume(d_left, d_right))
+            flush.fill_(r & 0xff)
+            rec("dual_mm", lambda: ctx.discrete(dmm_iters))
+            flush.fill_(r & 0xff)
+            rec("refinement", lambda: ctx.refine(pd_iters))
+    torch.cuda.synchronize()
+    out = {k: round(sum(a.elapsed_time(b) for a, b in v) / len(v), 4) for k, v in ev.items()}
+    out["refinement_iterations"] = pd_iters
+    return out
+
+
 def source_tag(kernel_file: str) -> str:
     """First 12 hex digits of the SHA-256 of a kernel's source file: a profile
     figure is used only while the kernel it was captured from is unchanged."""
@@ -1292,6 +1320,7 @@ def main():
     frame_bytes = survey_frame_bytes(H * W, L, 1, NI, NP, 5)
     roofline["frame_bytes"] = frame_bytes
     roofline["frame_frac"] = round(frame_bytes / (tot_ms / args.steps / 1e3) / 1e9 / peak, 4)
+    roofline["stage_ms"] = time_stages(ctx, d_left, d_right, NI, NP, flush, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

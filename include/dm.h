@@ -38,7 +38,9 @@
  *     are recorded in the workspace and reported by the next synchronising
  *     call: DM_ERR_RANGE for a dual outside the packed storage's range,
  *     DM_ERR_DEVICE otherwise (e.g. an edge weight with no integer penalty
- *     table).  No kernel waits on another, so DM_ERR_TIMEOUT is not returned.
+ *     table), DM_ERR_TIMEOUT when a bounded device-side wait gave up (the
+ *     grid barriers of the one-launch refinement; the kernel then returns and
+ *     the context stays usable, its refined disparity undefined).
  *   - The main stages open NVTX ranges named after their entry points.
  *   - A context is not thread-safe: use one context per host thread.
  */
@@ -99,7 +101,15 @@ typedef struct dm_params {
                             /* where its bounds hold, else int32                 */
     int32_t cost_bytes;     /* storage of the cost volume: 0 or 1 = uint8,       */
                             /* 2 = uint16                                        */
-    int32_t reserved[5];
+    int32_t pd_launch;      /* dm_refine: 0 = all iterations in one cooperative  */
+                            /* launch (grid barriers between iterations), 1 =    */
+                            /* one launch per iteration; same results bit for bit */
+    int32_t wait_test;      /* diagnostics, 0 in normal use: > 0 makes the first */
+                            /* grid barrier of the one-launch refinement wait for */
+                            /* that many arrivals that never come, so its wait   */
+                            /* (bounded to 20 ms in this mode, 1 s otherwise)    */
+                            /* gives up and DM_ERR_TIMEOUT is reported            */
+    int32_t reserved[3];
 } dm_params;
 
 typedef struct dm_ctx dm_ctx;
@@ -418,12 +428,19 @@ DM_API int dm_batch_discrete_pass(dm_batch* b, int which);
  *   which = 1: vertical chains, unaries d_lam_in (= lambda_h), d_wedge = wv,
  *              writes d_lam_out = lambda_v (d_cost may be NULL).
  * Layouts are those of the context API ([H][W][L] uint8 cost, [H][W] uint8
- * weights, [H][W][L] int32 duals); *p supplies the penalty.  d_err (nullable,
- * caller-zeroed device int32) receives nonzero bits if an edge weight has no
- * integer penalty table.  Asynchronous on `stream` (a cudaStream_t as void*).
- * Limit: 2 * H * W * KP * 4 bytes <= 32 MiB - 8.25 KiB, where KP is L rounded
- * up to 32, 64, 128 or 256; larger problems return DM_ERR_WORKSPACE before any
- * work is enqueued.  The first call on each device looks up the array's device
+ * weights, [H][W][L] int32 duals); *p supplies the penalty (checked as by
+ * dm_create; the pass always uses the hierarchical minorant and reads uint8
+ * costs, whatever p->cost_bytes says).  d_err (required, a caller-zeroed device
+ * int32) receives nonzero bits if an edge weight has no integer penalty table;
+ * d_lam_out must not be d_lam_in.  Asynchronous on `stream` (a cudaStream_t as
+ * void*).  The pass runs in int32: with P2 the largest omega C over every
+ * omega with a penalty table and n = max(H, W) + 1, it needs
+ * (255 + Lambda + 4 P2) n < 2^30 where Lambda bounds |d_lam_in|; the call
+ * returns DM_ERR_RANGE when this fails already for Lambda = 0 and relies on the
+ * caller for d_lam_in (the duals that Dual MM itself produces from such costs
+ * stay within it).  Limit: 2 * H * W * KP * 4 bytes <= 32 MiB - 8.25 KiB, where
+ * KP is L rounded up to 32, 64, 128 or 256; larger problems return
+ * DM_ERR_WORKSPACE before any work is enqueued.  The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture.  All calls share the one array: calls whose
  * work overlaps on the GPU race. */

@@ -89,6 +89,7 @@ bool params_ok(const dm_params& p)
         return false;
     if (p.warps < 1) return false;
     if (p.cost_bytes < 0 || p.cost_bytes > 2) return false;
+    if (p.pd_launch < 0 || p.pd_launch > 1 || p.wait_test < 0) return false;
     return true;
 }
 
@@ -253,8 +254,17 @@ int check_device_error(dm_ctx* c)
                           c->stream));
     DM_CK(cudaStreamSynchronize(c->stream));
     if (err == 0) return DM_OK;
-    // a dual outside the packed storage's range has its own code
-    return (err & dm::kDevErrRange) != 0 ? DM_ERR_RANGE : DM_ERR_DEVICE;
+    // a dual outside the packed storage's range and a wait that gave up have
+    // their own codes
+    if ((err & dm::kDevErrRange) != 0) return DM_ERR_RANGE;
+    if ((err & dm::kDevErrTimeout) != 0) {
+        // cleared once reported: the barriers of the next one-launch
+        // refinement give up as soon as they see it
+        DM_CK(cudaMemsetAsync(c->ws + c->lay.err, 0, sizeof(int32_t), c->stream));
+        DM_CK(cudaStreamSynchronize(c->stream));
+        return DM_ERR_TIMEOUT;
+    }
+    return DM_ERR_DEVICE;
 }
 
 int ready(const dm_ctx* c)
@@ -418,11 +428,13 @@ size_t base_bytes(const dm_ctx* c) { return ::base_bytes(c); }
 }  // namespace dm
 
 namespace dm {
-// Penalty taps of one edge weight (shared with the allocation-free entry point).
+// Penalty taps of one edge weight and the parameter check (shared with the
+// allocation-free entry point).
 int penalty_taps(int omega, int L, const dm_params& p, int32_t* row)
 {
     return build_taps(omega, L, p, row);
 }
+bool params_valid(const dm_params& p) { return params_ok(p); }
 }  // namespace dm
 
 extern "C" {
@@ -538,6 +550,7 @@ DM_API int dm_create(int H, int W, int L, const dm_params* p, dm_ctx** out)
     l.qv2 = add(HW * 4);
     l.epart = add(1024 * sizeof(double));
     l.err = add(sizeof(int32_t));
+    l.bar = add(sizeof(uint32_t));
     l.total = align_up(tot, 256);
     *out = c;
     return DM_OK;
@@ -756,13 +769,34 @@ DM_API int dm_refine(dm_ctx* ctx, int iters, const float* d_u0)
     dm::PdArgs a = pd_args(ctx);
     if (d_u0 != nullptr)
         DM_CK(cudaMemcpyAsync(a.u, d_u0, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
-    else
+    const int warps = ctx->p.warps;
+    if (ctx->p.pd_launch == 0) {
+        // every iteration in one cooperative launch (pd_run_kernel)
+        dm::PdRunArgs r{};
+        r.set[0] = a;
+        ctx->u_cur = ctx->pq_cur = 1;
+        r.set[1] = pd_args(ctx);
+        r.labels = d_u0 != nullptr ? nullptr
+                                   : reinterpret_cast<const uint16_t*>(ctx->ws + ctx->lay.labels);
+        r.iters = iters;
+        r.warps = warps;
+        r.bar = reinterpret_cast<unsigned*>(ctx->ws + ctx->lay.bar);
+        r.err = reinterpret_cast<int32_t*>(ctx->ws + ctx->lay.err);
+        r.bar_skew = ctx->p.wait_test;
+        r.wait_ns = ctx->p.wait_test > 0 ? 20000000LL : 1000000000LL;
+        DM_CK(cudaMemsetAsync(r.bar, 0, sizeof(unsigned), ctx->stream));
+        DM_CK(dm::launch_pd_run(r, ctx->stream));
+        ctx->launches += 1;
+        ctx->u_cur = ctx->pq_cur = iters & 1;
+        ctx->have_u = true;
+        return DM_OK;
+    }
+    if (d_u0 == nullptr)
         DM_CK(dm::launch_init_u_from_labels(
             reinterpret_cast<const uint16_t*>(ctx->ws + ctx->lay.labels), a.u, n, ctx->stream));
     for (float* s : {a.ph, a.pv, a.qh, a.qv, a.ph2, a.pv2, a.qh2, a.qv2})
         DM_CK(dm::launch_zero_f32(s, n, ctx->stream));
     ctx->launches += (d_u0 != nullptr ? 0 : 1) + 8;
-    const int warps = ctx->p.warps;
     const int base = iters / warps, extra = iters % warps;
     for (int w = 0; w < warps; ++w) {
         const int nit = base + (w < extra ? 1 : 0);
@@ -1317,7 +1351,14 @@ DM_API int dm_solve_lr(dm_ctx* left, dm_ctx* right, const uint8_t* d_left, const
     // right view: the mirrored pair through the unchanged path, on its own stream
     if ((rc = dm_cost_volume_mirrored(right, d_left, d_right))) return rc;
     if ((rc = dm_discrete(right, dmm_iters, nullptr))) return rc;
-    if ((rc = dm_refine(right, pd_iters, nullptr))) return rc;
+    // two one-launch refinements that may overlap would each hold resident
+    // CTAs at grid barriers: the forked view takes one launch per iteration
+    // (the same result bit for bit)
+    const int32_t pd_launch = right->p.pd_launch;
+    if (fork) right->p.pd_launch = 1;
+    rc = dm_refine(right, pd_iters, nullptr);
+    right->p.pd_launch = pd_launch;
+    if (rc) return rc;
     // left view, concurrently when the streams differ
     if ((rc = dm_solve(left, d_left, d_right, dmm_iters, pd_iters, nullptr))) return rc;
     if (fork) {

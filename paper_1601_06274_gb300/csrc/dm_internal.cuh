@@ -26,10 +26,11 @@ constexpr int kInf = 1 << 29;
 constexpr int kDevErrBadOmega = 1;
 constexpr int kDevErrRange = 2;
 constexpr int kDevErrIndex = 4;  // checked builds: an index outside its array (access skipped)
+constexpr int kDevErrTimeout = 8;  // a bounded device-side wait gave up
 
 struct Layout {
     size_t cost, census, img, wh, wv, lam_h, lam_v, fmsg, bmsg, labels, lb, taps, taps16;
-    size_t u, u_new, u0, s1, s2, lo, hi, ph, pv, qh, qv, ph2, pv2, qh2, qv2, epart, err;
+    size_t u, u_new, u0, s1, s2, lo, hi, ph, pv, qh, qv, ph2, pv2, qh2, qv2, epart, err, bar;
     size_t total;
 };
 
@@ -116,6 +117,19 @@ struct PdArgs {
     float* pv2;
     float* qh2;
     float* qv2;
+};
+
+// The whole refinement in one cooperative launch (pd.cu): both ping-pong sets
+// (set[1] is set[0] with u/u_new and p, q/p2, q2 swapped), the start, the
+// iteration count and the grid barrier.
+struct PdRunArgs {
+    PdArgs set[2];
+    const uint16_t* labels;  // nullable: u already holds the start
+    int iters, warps;
+    unsigned* bar;           // arrival counter, zero at launch
+    int32_t* err;            // kDevErrTimeout when a barrier wait gives up
+    long long wait_ns;       // bound of one barrier wait
+    int bar_skew;            // arrivals that never come (0; > 0 only to test the bound)
 };
 
 // Batched primal-dual kernels (pd.cu): two descriptors per pair (set 0 -> set 1
@@ -208,6 +222,8 @@ struct JvpArgs {
 
 // dm_abi.cu: row of taps for one omega; returns the window radius or -1
 int penalty_taps(int omega, int L, const dm_params& p, int32_t* row);
+// dm_abi.cu: the parameter check of dm_create
+bool params_valid(const dm_params& p);
 
 // cost.cu
 cudaError_t launch_census_edges(const uint8_t* left, const uint8_t* right, int H, int W, int win,
@@ -290,6 +306,7 @@ cudaError_t launch_theta_h_from_i32(const int32_t* lam_v, const void* cost, int 
 cudaError_t launch_init_u_from_labels(const uint16_t* labels, float* u, int n, cudaStream_t s);
 cudaError_t launch_linearise(const PdArgs& a, cudaStream_t s);
 cudaError_t launch_pd_iter(const PdArgs& a, cudaStream_t s);
+cudaError_t launch_pd_run(const PdRunArgs& r, cudaStream_t s);
 cudaError_t launch_pd_adjoint(const AdjArgs& a, cudaStream_t s);
 bool pd_tile_supported(int tx, int ty);
 cudaError_t launch_pd_batch(const PdBatchArgs& b, int tx, int ty, int grid, cudaStream_t s);

@@ -19,6 +19,10 @@
 // zeroes what must start at zero (the boundary messages) and rewrites
 // everything else before reading it.  Two calls whose work overlaps on the GPU
 // (different streams, or different host threads) race on the array.
+//
+// The penalty taps are built on the host and reach the array through the
+// parameters of a small kernel (passed by value), so no enqueued operation
+// reads host memory.
 
 #include <cstring>
 #include <mutex>
@@ -30,10 +34,19 @@ namespace {
 constexpr size_t kScratchBytes = size_t(32) << 20;  // 32 MiB
 constexpr int kMaxDevices = 64;
 constexpr size_t kTapsBytes = 256 * dm::kTapW * sizeof(int32_t);  // 8 KiB
-constexpr size_t kErrOffset = kTapsBytes;                        // one int32
 constexpr size_t kMsgOffset = kTapsBytes + 256;                  // 256-byte aligned
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+// the taps table, passed by value as a kernel parameter (8 KiB)
+struct TapsTable {
+    int32_t v[256 * dm::kTapW];
+};
+
+__global__ void store_taps_kernel(const TapsTable t, int32_t* dst)
+{
+    for (int i = threadIdx.x; i < 256 * dm::kTapW; i += blockDim.x) dst[i] = t.v[i];
+}
 
 std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
@@ -61,39 +74,44 @@ extern "C" DM_API int dm_discrete_pass_noalloc(int H, int W, int L, const dm_par
                                                const uint8_t* d_wedge, const int32_t* d_lam_in,
                                                int32_t* d_lam_out, int32_t* d_err, void* stream)
 {
-    if (p == nullptr || d_lam_in == nullptr || d_lam_out == nullptr || d_wedge == nullptr)
+    if (p == nullptr || d_lam_in == nullptr || d_lam_out == nullptr || d_wedge == nullptr ||
+        d_err == nullptr || d_lam_in == d_lam_out)
         return DM_ERR_ARG;
     if (which != 0 && which != 1) return DM_ERR_ARG;
     if (which == 0 && d_cost == nullptr) return DM_ERR_ARG;
     if (H < 1 || W < 1 || L < 2 || L > 256 || H > 65535 || W > 65535) return DM_ERR_ARG;
-    if (p->struct_size != sizeof(dm_params)) return DM_ERR_ARG;
+    if (!dm::params_valid(*p)) return DM_ERR_ARG;
     const int lpt = L <= 32 ? 1 : (L <= 64 ? 2 : (L <= 128 ? 4 : 8));
     const int KP = 32 * lpt;
     // fmsg and bmsg: one int32 message of KP labels per chain node each
     const size_t msg_bytes = (size_t)H * W * KP * sizeof(int32_t);
     if (kMsgOffset + 2 * msg_bytes > kScratchBytes) return DM_ERR_WORKSPACE;
 
-    // penalty taps for every omega, built on the host into a stack buffer
-    int32_t taps[256 * dm::kTapW];
+    // penalty taps for every omega, built on the host
+    TapsTable taps;
     int radius = 1;
+    long long p2_all = 0;  // the largest cap omega C over every usable omega
     for (int om = 0; om < 256; ++om) {
-        const int r = dm::penalty_taps(om, L, *p, &taps[om * dm::kTapW]);
+        int32_t* row = &taps.v[om * dm::kTapW];
+        const int r = dm::penalty_taps(om, L, *p, row);
         if (r < 0 && (om == p->w_hi || om == p->w_lo)) return DM_ERR_ARG;
         if (r > radius) radius = r;
+        if (row[dm::kTapValid] && row[dm::kTapP2] > p2_all) p2_all = row[dm::kTapP2];
     }
+    // the int32 kernel's messages stay below 2^30 when (largest unary + 4 omega C)
+    // times the chain length does; with the uint8 costs and lambda_in = 0 this is
+    // the bound the context path admits
+    const long long n = (H > W ? H : W) + 1;
+    if ((255LL + 4 * p2_all) * n >= (1LL << 30)) return DM_ERR_RANGE;
 
     void* base = nullptr;
     int rc = scratch_address(&base);
     if (rc != DM_OK) return rc;
     unsigned char* s = static_cast<unsigned char*>(base);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(s, taps, kTapsBytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return DM_ERR_CUDA;
     int32_t* err = d_err;
-    if (err == nullptr) {
-        err = reinterpret_cast<int32_t*>(s + kErrOffset);
-        if (cudaMemsetAsync(err, 0, sizeof(int32_t), st) != cudaSuccess) return DM_ERR_CUDA;
-    }
+    store_taps_kernel<<<1, 256, 0, st>>>(taps, reinterpret_cast<int32_t*>(s));
+    if (cudaGetLastError() != cudaSuccess) return DM_ERR_CUDA;
 
     dm::DmmArgs a{};
     a.which = which;

@@ -222,23 +222,15 @@ __device__ __forceinline__ void cp_wait()
 // The Msg step
 // ---------------------------------------------------------------------------
 
-// minimum of v over the group's lanes: one redux for a whole warp; for 8 or 16
-// lanes one full-warp redux per group (a redux over a partial mask is slower);
-// a butterfly for smaller groups
+// minimum of v over the group's lanes: one redux for a whole warp (the
+// latency-bound top levels); a butterfly of shuffles for smaller groups (the
+// throughput-bound lower levels: fewer instructions than one redux per group,
+// and a redux over a partial mask is slower still)
 template <int G>
 __device__ __forceinline__ int group_min(int v)
 {
     if constexpr (G == 32) {
         return __reduce_min_sync(kFull, v);
-    } else if constexpr (G >= 8) {
-        const int mine = (int)(threadIdx.x & 31) / G;
-        int r = v;
-#pragma unroll
-        for (int g = 0; g < 32 / G; ++g) {
-            const int t = __reduce_min_sync(kFull, mine == g ? v : INT_MAX);
-            r = mine == g ? t : r;
-        }
-        return r;
     } else {
 #pragma unroll
         for (int s = 1; s < G; s <<= 1) v = min(v, __shfl_xor_sync(kFull, v, s));
@@ -541,18 +533,24 @@ __device__ __forceinline__ Spine spine_bwd(int j, int b)
 // (minc, maxc their extremes); only the one step from minc on is predicated.
 // Every lane's share of a block's copies is fixed for the sweep: the same
 // chunks of the same rows, one block further on each time.
+//
+// `extra` more nodes past the last step are staged as well (the Handshake's two
+// nodes; they stay in the ring at sweep positions cnt_g and cnt_g + 1), and the
+// boundary message is read from message slot `mslot_in` after the first block
+// arrives (its copy must be committed before the call).
 template <class Y, int R>
 __device__ __forceinline__ void sweep(const Dmm16Args& A, const Ctx& C, const uint32_t* s_taps,
                                       const Lane<Y>& ln, int k0, int dir, int cnt_g, int minc, int maxc,
-                                      Msg<Y::NWL>& m, Spine sp)
+                                      int extra, int mslot_in, bool active, Msg<Y::NWL>& m, Spine sp)
 {
     using DT = typename Y::DT;
     using Gm = Geo<Y>;
     constexpr int NWL = Y::NWL, KBY = Y::KB, CH = Gm::ROW / 16;
-    if (maxc <= 0) return;
     uint8_t* sbuf = dir > 0 ? reinterpret_cast<uint8_t*>(A.fmsg) : reinterpret_cast<uint8_t*>(A.bmsg);
     int32_t* sofs = dir > 0 ? A.fofs : A.bofs;
-    const int nblk = (maxc + KBY - 1) / KBY;
+    const int nblk = (maxc + KBY - 1) / KBY;              // blocks with steps
+    const int nstg = (maxc + extra + KBY - 1) / KBY;      // blocks to stage
+    const int stg_g = active ? cnt_g + extra : 0;         // this group's staged nodes
     // copy plan: node u of block bi is node k0 + dir (KBY bi + u), pixel pix0 + pst (KBY bi + u)
     const int rowd = C.L * (int)sizeof(DT);
     const int pix0 = C.pix(k0);
@@ -561,8 +559,8 @@ __device__ __forceinline__ void sweep(const Dmm16Args& A, const Ctx& C, const ui
     const uint8_t* rsrc = reinterpret_cast<const uint8_t*>(A.delta_in) + (long long)pix0 * rowd;
     const int wsh = dir > 0 ? 0 : C.pstride();  // the crossed edge (k, k+1) or (k-1, k) by its left pixel
     auto issue = [&](int bi) {
-        const int cb = min(KBY, cnt_g - bi * KBY);
-        if (bi >= nblk || cb <= 0) return;
+        const int cb = min(KBY, stg_g - bi * KBY);
+        if (bi >= nstg || cb <= 0) return;
         uint8_t* blk = ln.ring + (bi % RB) * Gm::BLK;
         const uint8_t* src = rsrc + (long long)bi * KBY * rstep;
 #pragma unroll
@@ -574,10 +572,13 @@ __device__ __forceinline__ void sweep(const Dmm16Args& A, const Ctx& C, const ui
         for (int t = ln.q; t < 2 * cb; t += Y::G) {
             const int u = t >> 1;
             const int px = pix0 + pst * (bi * KBY + u);
+            const int k = k0 + dir * (bi * KBY + u);
             if ((t & 1) == 0) {
-                if (in_chain(C, k0 + dir * (bi * KBY + u), C.n)) cp_async<4>(blk + Gm::BASE_AT + 4 * u, A.base_in + px);
-            } else if (in_chain(C, k0 + dir * (bi * KBY + u) - (dir > 0 ? 0 : 1), C.n - 1)) {
-                cp_async<4>(blk + Gm::W_AT + 4 * u, A.wedge + ((px - wsh) & ~3));
+                if (in_chain(C, k, C.n)) cp_async<4>(blk + Gm::BASE_AT + 4 * u, A.base_in + px);
+            } else {
+                const int e = dir > 0 ? k : k - 1;  // the crossed edge (a staged extra node may have none)
+                if (e >= 0 && e < C.n - 1 && in_chain(C, e, C.n - 1))
+                    cp_async<4>(blk + Gm::W_AT + 4 * u, A.wedge + ((px - wsh) & ~3));
             }
         }
     };
@@ -586,6 +587,12 @@ __device__ __forceinline__ void sweep(const Dmm16Args& A, const Ctx& C, const ui
     for (int bi = 0; bi < RB - 1; ++bi) {  // RB - 1 commit groups, some possibly empty
         issue(bi);
         cp_commit();
+    }
+    if (nblk == 0) {  // no step: the staged nodes and the boundary message only
+        cp_wait<0>();
+        __syncwarp();
+        if (mslot_in >= 0) read_msg_slot(ln, mslot_in, m, active);
+        return;
     }
     // the step after which the next spine message is stored (its message enters
     // node k0 + dir (step + 1)); steps run in stretches that end at a spine
@@ -601,6 +608,7 @@ __device__ __forceinline__ void sweep(const Dmm16Args& A, const Ctx& C, const ui
     for (int bi = 0; bi < nblk; ++bi) {
         cp_wait<RB - 2>();
         __syncwarp();
+        if (bi == 0 && mslot_in >= 0) read_msg_slot(ln, mslot_in, m, active);
         const uint8_t* blk = ln.ring + (bi % RB) * Gm::BLK;
         const int s0 = bi * KBY;
         const int steps = min(KBY, maxc - s0);
@@ -707,27 +715,27 @@ __device__ __forceinline__ int slot_base(const Lane<Y>& ln, int i)
 }
 
 // Handshake over the edge (i, j) (Alg. Handshake) with the left message into i
-// (F) and the right message into j (B); the nodes are staged in slots si, sj.
-// Out: phi_ij (the left boundary message of the right part) and phi_ji (the
-// right boundary message of the left part).
+// (F) and the right message into j (B); the staged unary rows and bases of i
+// and j are given.  Out: phi_ij (the left boundary message of the right part)
+// and phi_ji (the right boundary message of the left part).
 template <class Y, int R>
-__device__ __forceinline__ void handshake(const Lane<Y>& ln, int si, int sj, const Taps& tp,
-                                          const Msg<Y::NWL>& F, const Msg<Y::NWL>& B, Msg<Y::NWL>& pij,
-                                          Msg<Y::NWL>& pji)
+__device__ __forceinline__ void handshake_at(const Lane<Y>& ln, const uint8_t* row_i, int base_i,
+                                             const uint8_t* row_j, int base_j, const Taps& tp,
+                                             const Msg<Y::NWL>& F, const Msg<Y::NWL>& B, Msg<Y::NWL>& pij,
+                                             Msg<Y::NWL>& pji)
 {
-    using Gm = Geo<Y>;
     constexpr int NWL = Y::NWL;
     uint32_t x[NWL];
     // message j -> i
     Msg<NWL> p1;
-    read_row<Y>(ln.ring + sj * Gm::ROW, ln, x);
-    p1.off = B.off + slot_base(ln, sj);
+    read_row<Y>(row_j, ln, x);
+    p1.off = B.off + base_j;
 #pragma unroll
     for (int p = 0; p < NWL; ++p) x[p] += B.v[p];
     msg_core<Y::G, NWL, R>(x, p1.v, p1.off, tp, ln.q);
     // half of the total min-marginal at i, shared to the right: floor(m_i / 2) - phi_ji
-    read_row<Y>(ln.ring + si * Gm::ROW, ln, x);
-    const int o_m = F.off + slot_base(ln, si) + p1.off;  // even
+    read_row<Y>(row_i, ln, x);
+    const int o_m = F.off + base_i + p1.off;  // even
 #pragma unroll
     for (int p = 0; p < NWL; ++p) {
         const uint32_t mi = F.v[p] + x[p] + p1.v[p];  // >= 0 and < 2^15 in both halves
@@ -747,6 +755,17 @@ __device__ __forceinline__ void handshake(const Lane<Y>& ln, int si, int sj, con
     for (int p = 0; p < NWL; ++p) x[p] = ln.pad ? kInf2 : vsub2(0u, pij.v[p]);
     pji.off = -pij.off;
     msg_core<Y::G, NWL, R>(x, pji.v, pji.off, tp, ln.q);
+}
+
+// the same with the nodes staged in the node slots si, sj
+template <class Y, int R>
+__device__ __forceinline__ void handshake(const Lane<Y>& ln, int si, int sj, const Taps& tp,
+                                          const Msg<Y::NWL>& F, const Msg<Y::NWL>& B, Msg<Y::NWL>& pij,
+                                          Msg<Y::NWL>& pji)
+{
+    using Gm = Geo<Y>;
+    handshake_at<Y, R>(ln, ln.ring + si * Gm::ROW, slot_base(ln, si), ln.ring + sj * Gm::ROW, slot_base(ln, sj),
+                       tp, F, B, pij, pji);
 }
 
 // one Msg of a staged node's unary plus an incoming message (a sweep step in registers)
@@ -951,43 +970,57 @@ __device__ __forceinline__ void task(const Dmm16Args& A, const Ctx& C, const uin
                                      const Lane<Y>& ln, int a, int b, int type, bool active, int mode)
 {
     using M = Msg<Y::NWL>;
+    using Gm = Geo<Y>;
     const int len = b - a + 1;
     const int i = a + ((len + 1) >> 1) - 1, j = i + 1;
     uint8_t* fm = reinterpret_cast<uint8_t*>(A.fmsg);
     uint8_t* bm = reinterpret_cast<uint8_t*>(A.bmsg);
-    // the inherited message(s) at the split go to message slot 0 (and 1) while the sweep runs
+    M m, inh, pij, pji;
     __syncwarp();
-    if (mode == 0) issue_msg<Y>(type ? bm : fm, type ? A.bofs : A.fofs, C, type ? j : i, ln, 0, active);
     if (mode == 2) {
+        // the root's Handshake: both messages into the split edge from memory
         issue_msg<Y>(fm, A.fofs, C, i, ln, 0, active);
         issue_msg<Y>(bm, A.bofs, C, j, ln, 1, active);
-    }
-    cp_commit();
-    M m;
-    if (mode != 2) {
-        load_msg<Y>(type ? fm : bm, type ? A.fofs : A.bofs, C, type ? a : b, ln, m, active);
+        cp_commit();
+        stage_slots<Y>(A, C, ln, active ? i : 0, active ? 2 : 0, false);
+        cp_wait<0>();
+        __syncwarp();
+        read_msg_slot(ln, 0, inh, active);
+        read_msg_slot(ln, 1, m, active);
+        const Taps tp = taps_of<R>(s_taps, slot_omega(ln, 0, C, active ? i : -1));
+        handshake<Y, R>(ln, 0, 1, tp, inh, m, pij, pji);
+    } else {
+        // the sweep's boundary message (slot 1) and, for a Handshake, the inherited
+        // message at the split (slot 0), in flight with the sweep's first blocks
+        issue_msg<Y>(type ? fm : bm, type ? A.fofs : A.bofs, C, type ? a : b, ln, 1, active);
+        if (mode == 0) issue_msg<Y>(type ? bm : fm, type ? A.bofs : A.fofs, C, type ? j : i, ln, 0, active);
+        cp_commit();
         const int count = active ? (type ? i - a : b - j) : 0;
         const int maxc = __reduce_max_sync(kFull, count);
         const int minc = __reduce_min_sync(kFull, active ? count : maxc);
-        sweep<Y, R>(A, C, s_taps, ln, type ? a : b, type ? 1 : -1, count, minc, maxc, m,
+        const int extra = mode == 0 ? 2 : 0;  // the Handshake's nodes follow the sweep's
+        sweep<Y, R>(A, C, s_taps, ln, type ? a : b, type ? 1 : -1, count, minc, maxc, extra, 1, active, m,
                     type ? spine_fwd(a, i) : spine_bwd(j, b));
         if (mode == 1) {
             store_msg<Y>(type ? fm : bm, type ? A.fofs : A.bofs, C, type ? i : j, ln, m, active);
-            cp_wait<0>();
             return;
         }
+        __syncwarp();
+        // the nodes after the sweep: i then j (forward), j then i (backward); the
+        // weight staged with the first of them is that of the edge (i, j)
+        const int p0 = count, p1 = count + 1;
+        const uint8_t* b0 = ln.ring + ((p0 / Y::KB) % RB) * Gm::BLK;
+        const uint8_t* b1 = ln.ring + ((p1 / Y::KB) % RB) * Gm::BLK;
+        const uint8_t* r0 = b0 + (p0 % Y::KB) * Gm::ROW;
+        const uint8_t* r1 = b1 + (p1 % Y::KB) * Gm::ROW;
+        const int base0 = *reinterpret_cast<const int*>(b0 + Gm::BASE_AT + 4 * (p0 % Y::KB));
+        const int base1 = *reinterpret_cast<const int*>(b1 + Gm::BASE_AT + 4 * (p1 % Y::KB));
+        const uint32_t ww = *reinterpret_cast<const uint32_t*>(b0 + Gm::W_AT + 4 * (p0 % Y::KB));
+        const Taps tp = taps_of<R>(s_taps, active ? omega_of(ww, C, i) : 0);
+        read_msg_slot(ln, 0, inh, active);
+        if (type) handshake_at<Y, R>(ln, r0, base0, r1, base1, tp, m, inh, pij, pji);  // F_i swept
+        else handshake_at<Y, R>(ln, r1, base1, r0, base0, tp, inh, m, pij, pji);       // B_j swept
     }
-    // the Handshake's nodes i and j
-    stage_slots<Y>(A, C, ln, active ? i : 0, active ? 2 : 0, false);
-    cp_wait<0>();
-    __syncwarp();
-    M inh;
-    read_msg_slot(ln, 0, inh, active);
-    if (mode == 2) read_msg_slot(ln, 1, m, active);
-    const Taps tp = taps_of<R>(s_taps, slot_omega(ln, 0, C, active ? i : -1));
-    M pij, pji;
-    if (mode == 2 || !type) handshake<Y, R>(ln, 0, 1, tp, inh, m, pij, pji);  // F_i inherited
-    else handshake<Y, R>(ln, 0, 1, tp, m, inh, pij, pji);                      // F_i swept
     store_msg<Y>(bm, A.bofs, C, i, ln, pji, active);
     store_msg<Y>(fm, A.fofs, C, j, ln, pij, active);
 }
@@ -1031,6 +1064,33 @@ __device__ __forceinline__ Lane<Y> make_lane(const Dmm16Args& A, uint8_t* areas,
     return ln;
 }
 
+__device__ __forceinline__ Ctx make_ctx(const Dmm16Args& A, int chain)
+{
+    Ctx C;
+    C.which = A.which;
+    C.H = A.H;
+    C.W = A.W;
+    C.L = A.L;
+    C.n = A.which == 0 ? A.W : A.H;
+    C.c = chain;
+    C.c16 = A.cost16 != nullptr;
+    C.err = A.err;
+    return C;
+}
+
+// A leaf block (group layout) as a call of its own: it needs the most registers
+// of the pass, and out of line it neither spills nor makes the sweeps spill.  The
+// arguments are the CTA's copy of the pass arguments in shared memory and plain
+// integers (a reference to the kernel parameters would force a local copy).
+template <int LP, typename DT, int R>
+__device__ __noinline__ void leaf_call(const Dmm16Args* A, const uint32_t* s_taps, uint8_t* areas,
+                                       long long* s_lb, int chain, int a, int len, int maxlen)
+{
+    constexpr int GD = LP / 16;
+    using YD = Lay<LP, GD, DT, KB>;
+    leaf_block<YD, R>(*A, make_ctx(*A, chain), s_taps, make_lane<YD>(*A, areas, GD), a, len, maxlen, s_lb);
+}
+
 // One chain (row `chain` of the horizontal pass, column of the vertical pass)
 // of Alg. Dual_MM's minorant computation by the whole CTA.
 //
@@ -1045,15 +1105,18 @@ __device__ __forceinline__ Lane<Y> make_lane(const Dmm16Args& A, uint8_t* areas,
 // longest segment among its own groups, which keeps its subtrees consistent
 // because no other warp touches them.
 template <int LP, typename DT, int R>
-__device__ __forceinline__ void chain_g(const Dmm16Args& A, int chain, uint8_t* smem, const uint32_t* s_taps)
+__device__ __forceinline__ void chain_g(const Dmm16Args& A, const Dmm16Args* s_args, int chain, uint8_t* smem,
+                                        const uint32_t* s_taps)
 {
     constexpr int GD = LP / 16;                 // lanes per group of the group layout
     constexpr bool WIDE = LP >= 64;             // a warp holds a message with >= 2 labels per lane
     using YD = Lay<LP, GD, DT, KB>;
-    using YW = Lay<LP, (WIDE ? 32 : GD), DT, (WIDE ? 2 * KB : KB)>;
+    // the whole-warp layout stages 16 steps per block where its ring fits, else 8
+    constexpr int ROOM = (32 / GD - 1) * Area<LP, DT>::GRP + RB * Area<LP, DT>::BLK;
+    constexpr int KBW = RB * (16 * LP * (int)sizeof(DT) + 8 * 16) <= ROOM ? 16 : 8;
+    using YW = Lay<LP, (WIDE ? 32 : GD), DT, (WIDE ? KBW : KB)>;
     // the whole-warp ring fits in front of the last area's message slots
-    static_assert(!WIDE || RB * Geo<YW>::BLK <= (32 / GD - 1) * Area<LP, DT>::GRP + RB * Area<LP, DT>::BLK,
-                  "whole-warp staging ring");
+    static_assert(!WIDE || RB * Geo<YW>::BLK <= ROOM, "whole-warp staging ring");
     using Ar = Area<LP, DT>;
     constexpr int NWARP = warps_of<GD>();
     constexpr int NG = NWARP * 32 / GD;         // groups per CTA
@@ -1062,15 +1125,7 @@ __device__ __forceinline__ void chain_g(const Dmm16Args& A, int chain, uint8_t* 
     constexpr int NWIDE = YW::G == 32 ? NWARP : NG;  // segments one round of the wide layout takes
     uint8_t* areas = smem + 256 * tap_words<R>() * 4;
     const int gd = (int)threadIdx.x / GD, qd = (int)(threadIdx.x & 31) % GD;  // group-layout group and lane
-    Ctx C;
-    C.which = A.which;
-    C.H = A.H;
-    C.W = A.W;
-    C.L = A.L;
-    C.n = A.which == 0 ? A.W : A.H;
-    C.c = chain;
-    C.c16 = A.cost16 != nullptr;
-    C.err = A.err;
+    const Ctx C = make_ctx(A, chain);
     const int n = C.n;
     uint8_t* gtail = areas + NG * Ar::GRP;
     uint32_t* s_stk = reinterpret_cast<uint32_t*>(gtail) + gd * kStack;
@@ -1177,7 +1232,7 @@ __device__ __forceinline__ void chain_g(const Dmm16Args& A, int chain, uint8_t* 
                 __syncwarp();
             }
         } else if (kind == 3) {
-            leaf_block<YD, R>(A, C, s_taps, make_lane<YD>(A, areas, GD), a, len, maxlen, s_lb);
+            leaf_call<LP, DT, R>(s_args, s_taps, areas, s_lb, chain, a, len, maxlen);
         }
         if (!dfs) {
             __syncthreads();
@@ -1193,7 +1248,8 @@ template <int LP, int R, typename DT>
 constexpr int smem_g()
 {
     constexpr int NG = warps_of<LP / 16>() * 32 / (LP / 16);
-    return 256 * tap_words<R>() * 4 + NG * (Area<LP, DT>::GRP + kStack * 4 + 8);
+    return 256 * tap_words<R>() * 4 + NG * (Area<LP, DT>::GRP + kStack * 4 + 8) +
+           (int)((sizeof(Dmm16Args) + 15) & ~(size_t)15);
 }
 
 // Launched with programmatic stream serialisation: the taps table (which no
@@ -1207,9 +1263,13 @@ __global__ void __launch_bounds__(warps_of<LP / 16>() * 32, 24 / warps_of<LP / 1
     uint32_t* s_taps = reinterpret_cast<uint32_t*>(smem);
     constexpr int TW = tap_words<R>();
     for (int t = threadIdx.x; t < 256 * TW; t += blockDim.x) s_taps[t] = A.taps16[(t / TW) * kTapW + t % TW];
+    // the arguments, for the leaf blocks' calls, at the end of the dynamic shared memory
+    Dmm16Args* s_args = reinterpret_cast<Dmm16Args*>(smem + smem_g<LP, R, DT>() -
+                                                     ((sizeof(Dmm16Args) + 15) & ~(size_t)15));
+    if (threadIdx.x == 0) *s_args = A;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     __syncthreads();
-    chain_g<LP, DT, R>(A, blockIdx.x, smem, s_taps);
+    chain_g<LP, DT, R>(A, s_args, blockIdx.x, smem, s_taps);
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 

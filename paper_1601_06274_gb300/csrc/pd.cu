@@ -277,6 +277,99 @@ __global__ void __launch_bounds__(kTX * kTY) pd_fused_kernel(const PdArgs A)
     allow_next_grid();
 }
 
+// --- the whole refinement in one cooperative launch -------------------------
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int* p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier number k (1, 2, ...) over all CTAs of a cooperative launch: one
+// arrival counter (zero at launch) that every CTA raises once per barrier and
+// waits to reach k * gridDim.x (+ the test skew).  The wait is bounded by
+// wait_ns of wall time; when it runs out, or another CTA has already given
+// up, the CTA records kDevErrTimeout and the caller returns.
+__device__ __forceinline__ bool grid_barrier(const PdRunArgs& R, unsigned k, int* s_go)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(R.bar, 1u);
+        const unsigned target = k * gridDim.x + (unsigned)R.bar_skew;
+        const unsigned long long t0 = global_ns();
+        int go = 1;
+        while (ld_acquire(R.bar) < target) {
+            if ((ld_relaxed(R.err) & kDevErrTimeout) != 0 ||
+                global_ns() - t0 > (unsigned long long)R.wait_ns) {
+                atomicOr(R.err, kDevErrTimeout);
+                go = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        *s_go = go;
+    }
+    __syncthreads();
+    return *s_go != 0;
+}
+
+// Every iteration of dm_refine in one launch: the start (u from the labels or
+// as given, zero duals), then per warp the linearisation and its iterations,
+// each a sweep of the CTAs over the tiles of pd_tile followed by a grid
+// barrier.  The arithmetic is pd_tile's and lin_one's, so the result is the
+// one of the launch-per-iteration form bit for bit.
+__global__ void __launch_bounds__(kTX * kTY) pd_run_kernel(const PdRunArgs R)
+{
+    __shared__ float s_un[kTY + 1][kTX + 1];
+    __shared__ float s_u[kTY + 1][kTX + 1];
+    __shared__ int s_go;
+    const PdArgs& A0 = R.set[0];
+    const int n = A0.H * A0.W;
+    const int tiles_x = (A0.W + kTX - 1) / kTX;
+    const int tiles = tiles_x * ((A0.H + kTY - 1) / kTY);
+    const int stride = gridDim.x * blockDim.x;
+    unsigned k = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (R.labels != nullptr) A0.u[i] = (float)R.labels[i];
+        A0.ph[i] = A0.pv[i] = A0.qh[i] = A0.qv[i] = 0.0f;
+        A0.ph2[i] = A0.pv2[i] = A0.qh2[i] = A0.qv2[i] = 0.0f;
+    }
+    if (!grid_barrier(R, ++k, &s_go)) return;
+    int cur = 0;
+    const int base = R.iters / R.warps, extra = R.iters % R.warps;
+    for (int w = 0; w < R.warps; ++w) {
+        const int nit = base + (w < extra ? 1 : 0);
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) lin_one(R.set[cur], i);
+        if (!grid_barrier(R, ++k, &s_go)) return;
+        for (int it = 0; it < nit; ++it) {
+            const PdArgs& A = R.set[cur];
+            for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+                pd_tile<kTX, kTY>(A, (t % tiles_x) * kTX, (t / tiles_x) * kTY, s_un, s_u);
+                __syncthreads();
+            }
+            if (!grid_barrier(R, ++k, &s_go)) return;
+            cur ^= 1;
+        }
+    }
+}
+
 // --- batched forms over many pairs (one launch per iteration for all pairs) ---
 
 // the pair whose range [start[p], start[p + 1]) holds t (start is ascending)
@@ -766,6 +859,42 @@ cudaError_t launch_pd_iter(const PdArgs& a, cudaStream_t s)
 {
     dim3 grd((a.W + kTX - 1) / kTX, (a.H + kTY - 1) / kTY);
     return launch_pdl(pd_fused_kernel, grd, dim3(kTX * kTY), s, a);
+}
+
+// CTAs of pd_run_kernel: as many as can be resident at once (the cooperative
+// launch checks it), at most one per tile; CTA b takes the tiles b, b + grid,
+// ..., so the SMs' tile counts differ by at most one CTA's extra tile
+int pd_run_grid(int H, int W)
+{
+    static int max_ctas = 0;
+    if (max_ctas == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pd_run_kernel, kTX * kTY, 0) !=
+                cudaSuccess)
+            return 0;
+        max_ctas = sms * per_sm;
+    }
+    const int tiles = ((W + kTX - 1) / kTX) * ((H + kTY - 1) / kTY);
+    return tiles < max_ctas ? tiles : max_ctas;
+}
+
+cudaError_t launch_pd_run(const PdRunArgs& r, cudaStream_t s)
+{
+    const int grid = pd_run_grid(r.set[0].H, r.set[0].W);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kTX * kTY);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pd_run_kernel, r);
 }
 
 template <int TX, int TY>

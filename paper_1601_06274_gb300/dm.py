@@ -37,7 +37,8 @@ class DmParams(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("tau", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("h", ctypes.c_double), ("warps", ctypes.c_int32),
                 ("dmm_path", ctypes.c_int32), ("cost_bytes", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("pd_launch", ctypes.c_int32), ("wait_test", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 _lib = None
@@ -734,8 +735,30 @@ def solve_lr(left, right, L: int, dmm_iters: int = 10, pd_iters: int = 100,
 def discrete_pass_noalloc(params: DmParams, which: int, cost, wedge, lam_in, lam_out,
                           err=None, stream=None):
     """dm_discrete_pass_noalloc: one Dual MM pass with no workspace and no
-    allocation inside the library (inputs/outputs are caller tensors)."""
+    allocation inside the library (inputs/outputs are caller tensors, all
+    contiguous on the current device: cost uint8 [H, W, L] (which = 0), wedge
+    uint8 [H, W], lam_in and lam_out int32 [H, W, L], distinct; err a zeroed
+    int32 tensor)."""
+    import torch
     H, W, L = lam_in.shape
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def need(t, dtype, shape, what):
+        if not (isinstance(t, torch.Tensor) and t.dtype == dtype and tuple(t.shape) == shape
+                and t.is_contiguous() and t.device == dev):
+            raise DMError(DM_ERR_ARG, f"dm_discrete_pass_noalloc: {what} must be a contiguous "
+                                      f"{dtype} tensor of shape {shape} on {dev}")
+    if which == 0 or cost is not None:
+        need(cost, torch.uint8, (H, W, L), "cost")
+    need(wedge, torch.uint8, (H, W), "wedge")
+    need(lam_in, torch.int32, (H, W, L), "lam_in")
+    need(lam_out, torch.int32, (H, W, L), "lam_out")
+    if err is None or not (isinstance(err, torch.Tensor) and err.dtype == torch.int32
+                           and err.numel() >= 1 and err.device == dev):
+        raise DMError(DM_ERR_ARG, "dm_discrete_pass_noalloc: err must be an int32 tensor on the "
+                                  "current device")
+    if lam_out.data_ptr() == lam_in.data_ptr():
+        raise DMError(DM_ERR_ARG, "dm_discrete_pass_noalloc: lam_out must not be lam_in")
     st = stream.cuda_stream if stream is not None else None
     _ck(lib().dm_discrete_pass_noalloc(H, W, L, ctypes.byref(params), int(which), _ptr(cost),
                                        _ptr(wedge), _ptr(lam_in), _ptr(lam_out), _ptr(err),

@@ -336,3 +336,61 @@ def test_adjoint_is_transpose_of_tangent_512x256x96(dm):
         worst = max(worst, abs(lhs - rhs) / float(prod.abs().sum()))
     print(f"dot-product identity: worst relative difference {worst:.2e}")
     assert worst <= 1e-4
+
+
+# Config 3's depth: 200 iterations, a checkpoint every 20, 5 warps.  The unrolled
+# map is kinked at the 1e-3 scale on almost every instance (see the module
+# docstring); in the convex regime (C -> infinity, so q = 0) with a weak
+# regulariser, some crops are smooth at that scale along nearly every
+# direction, and there the FP32 and FP64 trajectories take the same branches.
+# These two were found so by the same h / h/2 test the check applies.
+DEEP = [(4, 128, 96, 15), (6, 128, 96, 4)]   # H, W, L, seed
+
+
+@pytest.mark.parametrize("H,W,L,seed", DEEP)
+def test_gradient_at_200_iterations_matches_oracle_and_central_differences(dm, H, W, L, seed):
+    iters, ckpt, warps, lam, C = 200, 20, 5, 0.05, 1e7
+    sp = S.make_pair(H, W, L, planes=4, noise_sigma=2.0, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    cost = (O.cost_volume(sp.left, sp.right, L) + rng.uniform(0, 1, (H, W, L))).astype(np.float32)
+    wh, wv = O.edge_weights(sp.left)
+    alpha = rng.uniform(0.5, 1.5, (H, W)).astype(np.float32)
+    u0 = np.clip(np.argmin(cost, 2) + rng.uniform(-0.3, 0.3, (H, W)), 0.1, L - 1.1).astype(np.float32)
+    c64, a64, u064 = cost.astype(np.float64), alpha.astype(np.float64), u0.astype(np.float64)
+    whf, wvf = wh.astype(float), wv.astype(float)
+    P = O.Params(C=C, lambda_r=lam, warps=warps)
+    ru, _, _ = O.refine(c64, whf, wvf, u064, iters, P, a64)
+    gt = _away_from_ties(sp.gt, ru)
+    ou, _, ogc, oga, ogl = O.refine_grad(c64, whf, wvf, u064, iters, gt, P, a64)
+    ctx = dm.Context(H, W, L, dm.default_params(warps=warps, C=C))
+    ctx.set_cost_volume(np.zeros((H, W, L), np.uint8), wh, wv)
+    u, gc, ga, gl = _gpu_grad(dm, ctx, cost, alpha, lam, u0, iters, ckpt, gt)
+    # the FP32 trajectory stays on the FP64 one
+    assert np.abs(u - ou).max() <= U_TOL
+    # the GPU reverse mode against the oracle's FP64 reverse mode
+    assert _rel(gc, ogc) <= G_TOL
+    assert _rel(ga, oga) <= G_TOL
+    assert gl == pytest.approx(ogl, rel=G_TOL, abs=1e-7)
+    # 64 central differences at h = 1e-3 of the FP64 forward (BASELINE's check);
+    # a direction whose quotients at h and h/2 differ straddles a kink
+    def lossf(c, a, l):
+        uu = O.refine(c, whf, wvf, u064, iters, O.Params(C=C, lambda_r=l, warps=warps), a)[0]
+        return np.abs(uu - gt).mean()
+    drng = np.random.default_rng(7)
+    smooth, errs = 0, []
+    for _ in range(64):
+        v = drng.standard_normal(cost.size + alpha.size + 1)
+        v /= np.linalg.norm(v)
+        vc, va, vl = v[:cost.size].reshape(cost.shape), v[cost.size:-1].reshape(alpha.shape), v[-1]
+
+        def q(h):
+            return (lossf(c64 + h * vc, a64 + h * va, lam + h * vl)
+                    - lossf(c64 - h * vc, a64 - h * va, lam - h * vl)) / (2 * h)
+        f1, f2 = q(1e-3), q(5e-4)
+        if abs(f1 - f2) > 1e-4 * max(abs(f1), 1e-9):
+            continue
+        smooth += 1
+        an = float((gc * vc).sum() + (ga * va).sum() + gl * vl)
+        errs.append(abs(an - f1) / max(abs(f1), 1e-9))
+    assert smooth >= 56, f"only {smooth} of 64 directions free of kinks"
+    assert max(errs) <= G_TOL

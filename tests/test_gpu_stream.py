@@ -176,3 +176,44 @@ def test_stream_1920x1080x256_invariants(dm):
         rows = slice(500, 504)
         crop = O.cost_volume(sp.left[498:506], sp.right[498:506], L)[2:6]
         assert np.array_equal(_np(c[rows]).view(np.uint16).astype(np.int32), crop)
+
+
+@pytest.mark.parametrize("warm", [False, True])
+def test_stream_1920x1080x256_sampled_chains_bit_exact(dm, warm):
+    """One Dual MM iteration on the streaming frame (1920 x 1080, 256 labels,
+    uint16 costs) cold (frame 0) and warm-started (frame 1 from frame 0's
+    lambda_v): rows 0, 1, 540, 1079 of the horizontal pass and columns 0, 960,
+    1919 of the vertical pass against the oracle's hierarchical minorant of
+    those chains (App. A), bit for bit."""
+    spec = S.STREAM
+    H, W, L = spec["H"], spec["W"], spec["L"]
+    ctx = _ctx(dm, H, W, L)
+    frames = list(S.make_sequence(H, W, L, 2, planes=spec["planes"],
+                                  noise_sigma=spec["noise_sigma"], drift=spec["drift"], seed=0))
+    if warm:
+        ctx.solve(frames[0].left, frames[0].right, spec["dmm_iters"], spec["pd_iters"])
+        ctx.cost_volume_warm(frames[1].left, frames[1].right)
+    else:
+        ctx.cost_volume(frames[0].left, frames[0].right)
+    assert ctx.path()[0] == 8
+    c, wh_t, wv_t = ctx.cost()
+    wh, wv = _np(wh_t), _np(wv_t)
+    rows, cols = (0, 1, 540, 1079), (0, 960, 1919)
+    _, lv = ctx.duals()
+    lv_in = {y: _np(lv[y]).astype(np.int64) for y in rows}   # zero for the cold frame
+    c_rows = {y: _np(c[y]).view(np.uint16).astype(np.int64) for y in rows}
+    ctx.discrete_pass(0)
+    lh, _ = ctx.duals()
+    for y in rows:
+        V = np.stack([O.penalty_table(int(wh[y, x]), L) for x in range(W - 1)])
+        mu = O.hier_minorant(c_rows[y] + lv_in[y], V)
+        assert np.array_equal(_np(lh[y]).astype(np.int64) + lv_in[y], mu), f"row {y}"
+    lh_cols = {x: _np(lh[:, x]).astype(np.int64) for x in cols}
+    ctx.discrete_pass(1)
+    _, lv = ctx.duals()
+    for x in cols:
+        V = np.stack([O.penalty_table(int(wv[y, x]), L) for y in range(H - 1)])
+        nu = O.hier_minorant(lh_cols[x], V)
+        assert np.array_equal(_np(lv[:, x]).astype(np.int64) + lh_cols[x], nu), f"column {x}"
+    if not warm:
+        assert not any(np.any(v) for v in lv_in.values())

@@ -77,15 +77,44 @@ def test_noalloc_rejects_too_large_and_bad_arguments(dm):
     p = dm.default_params()
     lib = dm.lib()
     dummy = torch.zeros(16, dtype=torch.int32, device="cuda")
+    other = torch.zeros(16, dtype=torch.int32, device="cuda")
     ptr = ctypes.c_void_p(dummy.data_ptr())
+    optr = ctypes.c_void_p(other.data_ptr())
     # 2 * 256 * 256 * 128 * 4 bytes = 64 MiB > 32 MiB of fixed scratch
-    rc = lib.dm_discrete_pass_noalloc(256, 256, 128, ctypes.byref(p), 0, ptr, ptr, ptr, ptr, None,
+    rc = lib.dm_discrete_pass_noalloc(256, 256, 128, ctypes.byref(p), 0, ptr, ptr, ptr, optr, ptr,
                                       None)
     assert rc == dm.DM_ERR_WORKSPACE
-    assert lib.dm_discrete_pass_noalloc(8, 8, 16, ctypes.byref(p), 2, ptr, ptr, ptr, ptr, None,
+    assert lib.dm_discrete_pass_noalloc(8, 8, 16, ctypes.byref(p), 2, ptr, ptr, ptr, optr, ptr,
                                         None) == dm.DM_ERR_ARG
-    assert lib.dm_discrete_pass_noalloc(8, 8, 16, ctypes.byref(p), 0, None, ptr, ptr, ptr, None,
+    assert lib.dm_discrete_pass_noalloc(8, 8, 16, ctypes.byref(p), 0, None, ptr, ptr, optr, ptr,
                                         None) == dm.DM_ERR_ARG
     bad = dm.default_params(w_hi=3)
-    assert lib.dm_discrete_pass_noalloc(8, 8, 16, ctypes.byref(bad), 0, ptr, ptr, ptr, ptr, None,
+    assert lib.dm_discrete_pass_noalloc(8, 8, 16, ctypes.byref(bad), 0, ptr, ptr, ptr, optr, ptr,
                                         None) == dm.DM_ERR_ARG
+    # the error word is required, the output must not alias the input, and the
+    # parameters are checked as dm_create checks them
+    assert lib.dm_discrete_pass_noalloc(8, 8, 16, ctypes.byref(p), 0, ptr, ptr, ptr, optr, None,
+                                        None) == dm.DM_ERR_ARG
+    assert lib.dm_discrete_pass_noalloc(8, 8, 16, ctypes.byref(p), 0, ptr, ptr, ptr, ptr, ptr,
+                                        None) == dm.DM_ERR_ARG
+    neg = dm.default_params(tau=-1.0)
+    assert lib.dm_discrete_pass_noalloc(8, 8, 16, ctypes.byref(neg), 0, ptr, ptr, ptr, optr, ptr,
+                                        None) == dm.DM_ERR_ARG
+
+
+def test_noalloc_binding_checks_its_tensors(dm):
+    import torch
+    H, W, L = 6, 7, 16
+    p = dm.default_params()
+    cost = torch.zeros((H, W, L), dtype=torch.uint8, device="cuda")
+    wh = torch.zeros((H, W), dtype=torch.uint8, device="cuda")
+    lam = torch.zeros((H, W, L), dtype=torch.int32, device="cuda")
+    out = torch.empty_like(lam)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for args in [(cost.int(), wh, lam, out, err),               # cost of the wrong type
+                 (cost, wh[:, :-1], lam, out, err),              # weights of the wrong shape
+                 (cost, wh, lam.transpose(0, 1), out, err),      # not contiguous
+                 (cost, wh, lam, lam, err),                      # output aliases the input
+                 (cost, wh, lam, out, None)]:                    # no error word
+        with pytest.raises(dm.DMError):
+            dm.discrete_pass_noalloc(p, 0, *args)
