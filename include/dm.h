@@ -39,8 +39,9 @@
  *     call: DM_ERR_RANGE for a dual outside the packed storage's range,
  *     DM_ERR_DEVICE otherwise (e.g. an edge weight with no integer penalty
  *     table), DM_ERR_TIMEOUT when a bounded device-side wait gave up (the
- *     grid barriers of the one-launch refinement; the kernel then returns and
- *     the context stays usable, its refined disparity undefined).
+ *     waits between the iterations of the one-launch refinements; the kernel
+ *     then returns and the context stays usable, its refined disparity
+ *     undefined).
  *   - The main stages open NVTX ranges named after their entry points.
  *   - A context is not thread-safe: use one context per host thread.
  */
@@ -101,14 +102,17 @@ typedef struct dm_params {
                             /* where its bounds hold, else int32                 */
     int32_t cost_bytes;     /* storage of the cost volume: 0 or 1 = uint8,       */
                             /* 2 = uint16                                        */
-    int32_t pd_launch;      /* dm_refine: 0 = all iterations in one cooperative  */
-                            /* launch (grid barriers between iterations), 1 =    */
-                            /* one launch per iteration; same results bit for bit */
-    int32_t wait_test;      /* diagnostics, 0 in normal use: > 0 makes the first */
-                            /* grid barrier of the one-launch refinement wait for */
-                            /* that many arrivals that never come, so its wait   */
-                            /* (bounded to 20 ms in this mode, 1 s otherwise)    */
-                            /* gives up and DM_ERR_TIMEOUT is reported            */
+    int32_t pd_launch;      /* dm_refine: 0 = automatic: all iterations in one   */
+                            /* cooperative launch with the state in shared       */
+                            /* memory, one region per SM, where it fits, else 2; */
+                            /* 1 = one launch per iteration; 2 = one cooperative */
+                            /* launch, state in global memory, grid barriers.    */
+                            /* Same results bit for bit                          */
+    int32_t wait_test;      /* diagnostics, 0 in normal use: > 0 makes the waits */
+                            /* of the one-launch refinements wait for progress   */
+                            /* that never comes, so each wait (bounded to 20 ms  */
+                            /* in this mode, 1 s otherwise) gives up and         */
+                            /* DM_ERR_TIMEOUT is reported                         */
     int32_t reserved[3];
 } dm_params;
 

@@ -89,7 +89,7 @@ bool params_ok(const dm_params& p)
         return false;
     if (p.warps < 1) return false;
     if (p.cost_bytes < 0 || p.cost_bytes > 2) return false;
-    if (p.pd_launch < 0 || p.pd_launch > 1 || p.wait_test < 0) return false;
+    if (p.pd_launch < 0 || p.pd_launch > 2 || p.wait_test < 0) return false;
     return true;
 }
 
@@ -770,7 +770,36 @@ DM_API int dm_refine(dm_ctx* ctx, int iters, const float* d_u0)
     if (d_u0 != nullptr)
         DM_CK(cudaMemcpyAsync(a.u, d_u0, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
     const int warps = ctx->p.warps;
-    if (ctx->p.pd_launch == 0) {
+    dm::PdResPlan plan{};
+    if (ctx->p.pd_launch == 0 && dm::pd_res_plan(ctx->H, ctx->W, &plan)) {
+        // every iteration in one cooperative launch, the state in shared memory
+        // (pd_res_kernel)
+        dm::PdResArgs r{};
+        r.a = a;
+        r.labels = d_u0 != nullptr ? nullptr
+                                   : reinterpret_cast<const uint16_t*>(ctx->ws + ctx->lay.labels);
+        r.iters = iters;
+        r.warps = warps;
+        r.nx = plan.nx;
+        r.ny = plan.ny;
+        r.RW = plan.RW;
+        r.RH = plan.RH;
+        r.K = plan.K;
+        r.EW = plan.EW;
+        r.EH = plan.EH;
+        r.TR = plan.TR;
+        r.bar = reinterpret_cast<unsigned*>(ctx->ws + ctx->lay.bar);
+        r.err = reinterpret_cast<int32_t*>(ctx->ws + ctx->lay.err);
+        r.wait_skew = ctx->p.wait_test;
+        r.wait_ns = ctx->p.wait_test > 0 ? 20000000LL : 1000000000LL;
+        DM_CK(cudaMemsetAsync(r.bar, 0, sizeof(unsigned), ctx->stream));
+        DM_CK(dm::launch_pd_res(r, plan, ctx->stream));
+        ctx->launches += 1;
+        ctx->u_cur = ctx->pq_cur = dm::pd_res_result_set(iters, warps, plan.K);
+        ctx->have_u = true;
+        return DM_OK;
+    }
+    if (ctx->p.pd_launch == 0 || ctx->p.pd_launch == 2) {
         // every iteration in one cooperative launch (pd_run_kernel)
         dm::PdRunArgs r{};
         r.set[0] = a;

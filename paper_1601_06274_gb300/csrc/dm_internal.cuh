@@ -132,6 +132,33 @@ struct PdRunArgs {
     int bar_skew;            // arrivals that never come (0; > 0 only to test the bound)
 };
 
+// The whole refinement with the state resident in shared memory (pd.cu): the
+// image is cut into nx x ny regions of RW x RH pixels, one CTA each.  A CTA
+// holds its region and a K-pixel margin from its neighbours (EW x EH at most)
+// and runs up to K iterations on it between exchanges; an exchange writes each
+// region's K-wide border into one of the two workspace state sets (by the
+// exchange's parity), passes a grid barrier and reads the margins back.
+struct PdResArgs {
+    PdArgs a;                // cost, weights, parameters, both state sets, u0, s1, s2
+    const uint16_t* labels;  // nullable: a.u already holds the start
+    int iters, warps;
+    int nx, ny, RW, RH, K, EW, EH, TR;  // regions, margin, stored area, rows per thread round
+    unsigned* bar;           // arrival counter, zero at launch
+    int32_t* err;            // kDevErrTimeout when a barrier wait gives up
+    long long wait_ns;       // bound of one barrier wait
+    int wait_skew;           // arrivals that never come (0; > 0 only to test the bound)
+};
+
+// launch shape of pd_res_kernel (pd_res_plan)
+struct PdResPlan {
+    int nx, ny, RW, RH, K, EW, EH, TR, threads;
+    size_t smem;
+};
+
+// the state set (0: u, ph, pv, qh, qv; 1: u_new, ph2, ...) that holds the
+// result of pd_res_kernel: the parity of its number of exchanges
+int pd_res_result_set(int iters, int warps, int K);
+
 // Batched primal-dual kernels (pd.cu): two descriptors per pair (set 0 -> set 1
 // and set 1 -> set 0), the first tile and the first pixel of each pair.
 struct PdBatchArgs {
@@ -307,6 +334,8 @@ cudaError_t launch_init_u_from_labels(const uint16_t* labels, float* u, int n, c
 cudaError_t launch_linearise(const PdArgs& a, cudaStream_t s);
 cudaError_t launch_pd_iter(const PdArgs& a, cudaStream_t s);
 cudaError_t launch_pd_run(const PdRunArgs& r, cudaStream_t s);
+bool pd_res_plan(int H, int W, PdResPlan* plan);
+cudaError_t launch_pd_res(const PdResArgs& r, const PdResPlan& plan, cudaStream_t s);
 cudaError_t launch_pd_adjoint(const AdjArgs& a, cudaStream_t s);
 bool pd_tile_supported(int tx, int ty);
 cudaError_t launch_pd_batch(const PdBatchArgs& b, int tx, int ty, int grid, cudaStream_t s);

@@ -16,6 +16,7 @@
 // The cost samples are uint8 (census) or float32 (a caller's cost volume), the
 // data weight a scalar or a per-pixel map.
 
+#include <algorithm>
 #include <utility>
 
 #include "dm_internal.cuh"
@@ -199,6 +200,21 @@ __device__ __forceinline__ float u_hat(const float* u, const float* ph, const fl
     return __fmaf_rn(-tau, div, u[i]);
 }
 
+// the same from values: (ph, qh) of the edges to the right (r) and from the
+// left (l), (pv, qv) of the edges down (d) and from above (a); a flag is false
+// where the image has no such edge.  Same operations in the same order.
+__device__ __forceinline__ float u_hat_v(float u, bool r, float ph_r, float qh_r, bool l,
+                                         float ph_l, float qh_l, bool d, float pv_d, float qv_d,
+                                         bool a, float pv_a, float qv_a, float tau)
+{
+    float div = 0.0f;
+    if (r) div = __fadd_rn(div, __fsub_rn(ph_r, qh_r));
+    if (l) div = __fsub_rn(div, __fsub_rn(ph_l, qh_l));
+    if (d) div = __fadd_rn(div, __fsub_rn(pv_d, qv_d));
+    if (a) div = __fsub_rn(div, __fsub_rn(pv_a, qv_a));
+    return __fmaf_rn(-tau, div, u);
+}
+
 // prox of tau times the linearised data term before the box clamp; *cs is the
 // case taken: 0 above the kink, 1 below it, 2 at the kink u0
 __device__ __forceinline__ float prox_lin(float uh, float u0, float s1, float s2, float tau, int* cs)
@@ -305,19 +321,20 @@ __device__ __forceinline__ int ld_relaxed(const int* p)
 // waits to reach k * gridDim.x (+ the test skew).  The wait is bounded by
 // wait_ns of wall time; when it runs out, or another CTA has already given
 // up, the CTA records kDevErrTimeout and the caller returns.
-__device__ __forceinline__ bool grid_barrier(const PdRunArgs& R, unsigned k, int* s_go)
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int32_t* err, int skew,
+                                             long long wait_ns, unsigned k, int* s_go)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        atomicAdd(R.bar, 1u);
-        const unsigned target = k * gridDim.x + (unsigned)R.bar_skew;
+        atomicAdd(bar, 1u);
+        const unsigned target = k * gridDim.x + (unsigned)skew;
         const unsigned long long t0 = global_ns();
         int go = 1;
-        while (ld_acquire(R.bar) < target) {
-            if ((ld_relaxed(R.err) & kDevErrTimeout) != 0 ||
-                global_ns() - t0 > (unsigned long long)R.wait_ns) {
-                atomicOr(R.err, kDevErrTimeout);
+        while (ld_acquire(bar) < target) {
+            if ((ld_relaxed(err) & kDevErrTimeout) != 0 ||
+                global_ns() - t0 > (unsigned long long)wait_ns) {
+                atomicOr(err, kDevErrTimeout);
                 go = 0;
                 break;
             }
@@ -351,24 +368,231 @@ __global__ void __launch_bounds__(kTX * kTY) pd_run_kernel(const PdRunArgs R)
         A0.ph[i] = A0.pv[i] = A0.qh[i] = A0.qv[i] = 0.0f;
         A0.ph2[i] = A0.pv2[i] = A0.qh2[i] = A0.qv2[i] = 0.0f;
     }
-    if (!grid_barrier(R, ++k, &s_go)) return;
+    if (!grid_barrier(R.bar, R.err, R.bar_skew, R.wait_ns, ++k, &s_go)) return;
     int cur = 0;
     const int base = R.iters / R.warps, extra = R.iters % R.warps;
     for (int w = 0; w < R.warps; ++w) {
         const int nit = base + (w < extra ? 1 : 0);
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) lin_one(R.set[cur], i);
-        if (!grid_barrier(R, ++k, &s_go)) return;
+        if (!grid_barrier(R.bar, R.err, R.bar_skew, R.wait_ns, ++k, &s_go)) return;
         for (int it = 0; it < nit; ++it) {
             const PdArgs& A = R.set[cur];
             for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
                 pd_tile<kTX, kTY>(A, (t % tiles_x) * kTX, (t / tiles_x) * kTY, s_un, s_u);
                 __syncthreads();
             }
-            if (!grid_barrier(R, ++k, &s_go)) return;
+            if (!grid_barrier(R.bar, R.err, R.bar_skew, R.wait_ns, ++k, &s_go)) return;
             cur ^= 1;
         }
     }
 }
+
+// --- the whole refinement with the state in shared memory ---------------------
+
+// shared-memory bytes of pd_res_kernel for a stored area of EW x EH pixels:
+// nine float arrays (u, u+, u0, s1, s2, ph, pv, qh, qv) and two weight bytes
+__host__ __device__ constexpr size_t res_smem_bytes(int EW, int EH)
+{
+    return (size_t)EW * EH * (9 * sizeof(float) + 2) + 16;
+}
+
+// One CTA per region.  The CTA stores its region R and a margin of K pixels
+// on each side that has a neighbouring region (the area E), and runs an epoch
+// of up to K iterations on E alone: at step t (1..K) u+ is computed on E less
+// t pixels on the left and upper margins and t - 1 on the right and lower ones
+// (u_step's arithmetic, from values in shared memory), then q+, p+ on E less t
+// on every margin (pd_tile's arithmetic).  Each step needs only values the
+// previous step left valid, and after K steps R is exact.  Between epochs the
+// regions exchange their K-wide borders through the workspace state set of
+// the exchange's parity and a grid barrier; the other set still holds the
+// previous exchange, which a CTA behind by one barrier may be reading.  Every
+// warp of the refinement starts an epoch, whose first act is the
+// linearisation of E.  Results equal pd_tile's bit for bit.
+__global__ void pd_res_kernel(const PdResArgs R)
+{
+    extern __shared__ float4 res_dyn[];
+    __shared__ int s_go;
+    const PdArgs& A = R.a;
+    const int W = A.W, H = A.H, K = R.K, EW = R.EW, NE = R.EW * R.EH;
+    const int rxi = blockIdx.x % R.nx, ryi = blockIdx.x / R.nx;
+    const int x0 = rxi * R.RW, y0 = ryi * R.RH;
+    const int w_eff = min(R.RW, W - x0), h_eff = min(R.RH, H - y0);
+    // E in image coordinates; a side shrinks during an epoch unless it is the
+    // image's border
+    const int ex0 = rxi > 0 ? x0 - K : 0, ey0 = ryi > 0 ? y0 - K : 0;
+    const int ex1 = min(W, x0 + w_eff + (rxi + 1 < R.nx ? K : 0));
+    const int ey1 = min(H, y0 + h_eff + (ryi + 1 < R.ny ? K : 0));
+    const int ew = ex1 - ex0, eh = ey1 - ey0;
+    const int shL = ex0 > 0, shR = ex1 < W, shU = ey0 > 0, shD = ey1 < H;
+    // region R inside E
+    const int rx0 = x0 - ex0, ry0 = y0 - ey0;
+    float* su = reinterpret_cast<float*>(res_dyn);
+    float* sun = su + NE;
+    float* const su0 = sun + NE;
+    float* const ss1 = su0 + NE;
+    float* const ss2 = ss1 + NE;
+    float* const sph = ss2 + NE;
+    float* const spv = sph + NE;
+    float* const sqh = spv + NE;
+    float* const sqv = sqh + NE;
+    uint8_t* const swh = reinterpret_cast<uint8_t*>(sqv + NE);
+    uint8_t* const swv = swh + NE;
+    const int TR = R.TR;
+    const int tx = threadIdx.x % EW, ty = threadIdx.x / EW;
+    const bool on = (int)threadIdx.x < EW * TR;
+    const float tau = A.tau, sigma = A.sigma, h = A.h, top = (float)(A.L - 1);
+    // the workspace state sets: 0 = (u, ph, pv, qh, qv), 1 = (u_new, ph2, ...)
+    auto set_u = [&](int k) { return k ? A.u_new : A.u; };
+    auto set_ph = [&](int k) { return k ? A.ph2 : A.ph; };
+    auto set_pv = [&](int k) { return k ? A.pv2 : A.pv; };
+    auto set_qh = [&](int k) { return k ? A.qh2 : A.qh; };
+    auto set_qv = [&](int k) { return k ? A.qv2 : A.qv; };
+
+    // start on all of E: u from the labels (or as given), zero duals
+    if (on && tx < ew)
+        for (int ey = ty; ey < eh; ey += TR) {
+            const int p = ey * EW + tx, i = (ey0 + ey) * W + ex0 + tx;
+            su[p] = R.labels != nullptr ? (float)R.labels[i] : A.u[i];
+            sph[p] = spv[p] = sqh[p] = sqv[p] = 0.0f;
+            swh[p] = A.wh[i];
+            swv[p] = A.wv[i];
+        }
+    __syncthreads();
+
+    const CostSrc cs = cost_src(A);
+    unsigned nbar = 0;   // grid barriers passed
+    int nex = 0;         // exchanges done
+    bool first = true;
+    const int base = R.iters / R.warps, extra = R.iters % R.warps;
+    for (int w = 0; w < R.warps; ++w) {
+        const int nit = base + (w < extra ? 1 : 0);
+        for (int done = 0; done < nit;) {
+            const int steps = min(K, nit - done);
+            if (!first) {
+                // exchange: R's K-wide border out, barrier, the margins of E in
+                const int sp = nex & 1;
+                if (on && tx >= rx0 && tx < rx0 + w_eff)
+                    for (int ey = ry0 + ty; ey < ry0 + h_eff; ey += TR) {
+                        const int rx = tx - rx0, ry = ey - ry0;
+                        if (rx >= K && rx < w_eff - K && ry >= K && ry < h_eff - K) continue;
+                        const int p = ey * EW + tx, i = (ey0 + ey) * W + ex0 + tx;
+                        __stcg(set_u(sp) + i, su[p]);
+                        __stcg(set_ph(sp) + i, sph[p]);
+                        __stcg(set_pv(sp) + i, spv[p]);
+                        __stcg(set_qh(sp) + i, sqh[p]);
+                        __stcg(set_qv(sp) + i, sqv[p]);
+                    }
+                if (!grid_barrier(R.bar, R.err, R.wait_skew, R.wait_ns, ++nbar, &s_go)) return;
+                if (on && tx < ew)
+                    for (int ey = ty; ey < eh; ey += TR) {
+                        if (tx >= rx0 && tx < rx0 + w_eff && ey >= ry0 && ey < ry0 + h_eff) continue;
+                        const int p = ey * EW + tx, i = (ey0 + ey) * W + ex0 + tx;
+                        su[p] = __ldcg(set_u(sp) + i);
+                        sph[p] = __ldcg(set_ph(sp) + i);
+                        spv[p] = __ldcg(set_pv(sp) + i);
+                        sqh[p] = __ldcg(set_qh(sp) + i);
+                        sqv[p] = __ldcg(set_qv(sp) + i);
+                    }
+                ++nex;
+                __syncthreads();
+            }
+            first = false;
+            if (done == 0) {
+                // the warp's linearisation of E around its current u (lin_one)
+                if (on && tx < ew)
+                    for (int ey = ty; ey < eh; ey += TR) {
+                        const int p = ey * EW + tx, i = (ey0 + ey) * W + ex0 + tx;
+                        const float u0 = su[p];
+                        const LinPx l = lin_px(cs, A.L, i, alpha_of(A.alpha_px, A.alpha, i), u0, h);
+                        float s1 = l.s1, s2 = l.s2;
+                        if (s2 < s1) {
+                            s1 = 0.5f * __fadd_rn(s1, s2);
+                            s2 = s1;
+                        }
+                        su0[p] = u0;
+                        ss1[p] = s1;
+                        ss2[p] = s2;
+                    }
+                __syncthreads();
+            }
+            for (int t = 1; t <= steps; ++t) {
+                // u+ on E less t (left, upper) and t - 1 (right, lower)
+                {
+                    const int xa = shL * t, xb = ew - shR * (t - 1);
+                    const int ya = shU * t, yb = eh - shD * (t - 1);
+                    if (on && tx >= xa && tx < xb)
+                        for (int ey = ya + ty; ey < yb; ey += TR) {
+                            const int p = ey * EW + tx, x = ex0 + tx, y = ey0 + ey;
+                            const bool l = x > 0, a = y > 0;
+                            const float uh = u_hat_v(su[p], x + 1 < W, sph[p], sqh[p], l,
+                                                     l ? sph[p - 1] : 0.0f, l ? sqh[p - 1] : 0.0f,
+                                                     y + 1 < H, spv[p], sqv[p], a,
+                                                     a ? spv[p - EW] : 0.0f, a ? sqv[p - EW] : 0.0f,
+                                                     tau);
+                            const float u0 = su0[p];
+                            int cse;
+                            const float v = prox_lin(uh, u0, ss1[p], ss2[p], tau, &cse);
+                            sun[p] = fminf(fmaxf(v, fmaxf(__fsub_rn(u0, h), 0.0f)),
+                                           fminf(__fadd_rn(u0, h), top));
+                        }
+                }
+                __syncthreads();
+                // q+, p+ on E less t on every shrinking side
+                {
+                    const int xa = shL * t, xb = ew - shR * t;
+                    const int ya = shU * t, yb = eh - shD * t;
+                    if (on && tx >= xa && tx < xb)
+                        for (int ey = ya + ty; ey < yb; ey += TR) {
+                            const int p = ey * EW + tx, x = ex0 + tx, y = ey0 + ey;
+                            const float ui = su[p], uni = sun[p];
+                            if (x + 1 < W) {
+                                const float om = __fmul_rn(A.lambda_r, (float)swh[p]);
+                                const float uj = su[p + 1], unj = sun[p + 1];
+                                sqh[p] = prox_conj(q_arg(sqh[p], tau, ui, uj), om, 0.0f, A.bq, tau);
+                                sph[p] = prox_conj(p_arg(sph[p], sigma, ui, uni, uj, unj), om, A.ap,
+                                                   A.bp, sigma);
+                            }
+                            if (y + 1 < H) {
+                                const float om = __fmul_rn(A.lambda_r, (float)swv[p]);
+                                const float uj = su[p + EW], unj = sun[p + EW];
+                                sqv[p] = prox_conj(q_arg(sqv[p], tau, ui, uj), om, 0.0f, A.bq, tau);
+                                spv[p] = prox_conj(p_arg(spv[p], sigma, ui, uni, uj, unj), om, A.ap,
+                                                   A.bp, sigma);
+                            }
+                        }
+                }
+                __syncthreads();
+                float* const tmp = su;
+                su = sun;
+                sun = tmp;
+            }
+            done += steps;
+        }
+    }
+    // R's state into the set after the last exchange's (nobody reads it any
+    // more), its linearisation into u0, s1, s2
+    // with no exchange and a start given in set 0, another CTA may still be
+    // reading its margin of that start
+    if (nex == 0 && R.labels == nullptr && R.iters > 0 && gridDim.x > 1)
+        if (!grid_barrier(R.bar, R.err, R.wait_skew, R.wait_ns, ++nbar, &s_go)) return;
+    const int fs = nex & 1;
+    const bool lin = R.iters > 0;
+    if (on && tx >= rx0 && tx < rx0 + w_eff)
+        for (int ey = ry0 + ty; ey < ry0 + h_eff; ey += TR) {
+            const int p = ey * EW + tx, i = (ey0 + ey) * W + ex0 + tx;
+            set_u(fs)[i] = su[p];
+            set_ph(fs)[i] = sph[p];
+            set_pv(fs)[i] = spv[p];
+            set_qh(fs)[i] = sqh[p];
+            set_qv(fs)[i] = sqv[p];
+            if (lin) {
+                A.u0[i] = su0[p];
+                A.s1[i] = ss1[p];
+                A.s2[i] = ss2[p];
+            }
+        }
+}
+
 
 // --- batched forms over many pairs (one launch per iteration for all pairs) ---
 
@@ -895,6 +1119,94 @@ cudaError_t launch_pd_run(const PdRunArgs& r, cudaStream_t s)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, pd_run_kernel, r);
+}
+
+// Regions of pd_res_kernel: at most one per SM and about 1024 pixels or more
+// each; among the region grids nx x ny that fit, the one with the smallest
+// region (then the shortest boundary).  The margin K is kResK, or less where a
+// region is thinner.  False when the stored area does not fit in shared memory
+// (or one of its rows in one CTA): the caller takes pd_run_kernel instead.
+constexpr int kResK = 5;
+
+bool pd_res_plan(int H, int W, PdResPlan* plan)
+{
+    static int sms = 0, max_smem = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+                cudaSuccess) {
+            sms = 0;
+            return false;
+        }
+    }
+    const long long px = (long long)H * W;
+    const int want = (int)std::min<long long>(sms, std::max<long long>(1, (px + 1023) / 1024));
+    long long best_area = -1, best_per = 0;
+    // first only grids whose split axes keep regions at least kResK wide
+    for (int thin = 0; thin < 2 && best_area < 0; ++thin)
+        for (int nx = 1; nx <= std::min(W, want); ++nx) {
+            const int ny0 = std::min(H, want / nx);
+            if (ny0 < 1) break;
+            const int RW = (W + nx - 1) / nx, RH = (H + ny0 - 1) / ny0;
+            if (!thin && ((nx > 1 && RW < kResK) || (ny0 > 1 && RH < kResK))) continue;
+            const long long area = (long long)RW * RH, per = RW + RH;
+            if (best_area < 0 || area < best_area || (area == best_area && per < best_per)) {
+                best_area = area;
+                best_per = per;
+                plan->RW = RW;
+                plan->RH = RH;
+            }
+        }
+    if (best_area < 0) return false;
+    plan->nx = (W + plan->RW - 1) / plan->RW;
+    plan->ny = (H + plan->RH - 1) / plan->RH;
+    int K = kResK;
+    if (plan->nx > 1) K = std::min(K, plan->RW);
+    if (plan->ny > 1) K = std::min(K, plan->RH);
+    plan->K = K;
+    plan->EW = plan->RW + (plan->nx > 1 ? 2 * K : 0);
+    plan->EH = plan->RH + (plan->ny > 1 ? 2 * K : 0);
+    if (plan->EW > 1024) return false;
+    plan->smem = res_smem_bytes(plan->EW, plan->EH);
+    if (plan->smem > (size_t)max_smem) return false;
+    plan->TR = std::min(plan->EH, 1024 / plan->EW);
+    plan->threads = (plan->EW * plan->TR + 31) / 32 * 32;
+    return plan->nx * plan->ny <= sms;
+}
+
+int pd_res_result_set(int iters, int warps, int K)
+{
+    const int base = iters / warps, extra = iters % warps;
+    int epochs = 0;
+    for (int w = 0; w < warps; ++w) {
+        const int nit = base + (w < extra ? 1 : 0);
+        epochs += (nit + K - 1) / K;
+    }
+    return epochs > 1 ? (epochs - 1) & 1 : 0;
+}
+
+cudaError_t launch_pd_res(const PdResArgs& r, const PdResPlan& plan, cudaStream_t s)
+{
+    static size_t smem_set = 0;   // the opt-in is raised once per larger size
+    if (plan.smem > smem_set) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            pd_res_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+        if (e != cudaSuccess) return e;
+        smem_set = plan.smem;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(plan.nx * plan.ny);
+    cfg.blockDim = dim3(plan.threads);
+    cfg.dynamicSmemBytes = plan.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pd_res_kernel, r);
 }
 
 template <int TX, int TY>
