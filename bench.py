@@ -433,6 +433,18 @@ def time_stages(ctx, d_left, d_right, dmm_iters, pd_iters, flush, stream, reps=5
     return out
 
 
+def refinement_issue(ms, iters):
+    """The refinement's single launch against the instruction-issue bound: warp
+    instructions of its ncu capture (null once pd.cu has changed) over the
+    stage's measured time."""
+    inst = NCU_PD_INSTRUCTIONS.get(("pd_res_kernel", iters, source_tag("pd.cu")))
+    out = {"kernel": "pd_res_kernel", "bound": "issue", "ms": ms,
+           "warp_instructions_per_launch": inst, "issue_frac": None}
+    if inst is not None and ms > 0:
+        out["issue_frac"] = round(inst / (ms / 1e3) / 1e9 / ISSUE_PEAK_GINST_S, 4)
+    return out
+
+
 def source_tag(kernel_file: str) -> str:
     """First 12 hex digits of the SHA-256 of a kernel's source file: a profile
     figure is used only while the kernel it was captured from is unchanged."""
@@ -477,6 +489,9 @@ KERNEL_FILES = {8: "dmg_impl.cuh", 16: "dmm16_impl.cuh", 32: "dmm.cu"}
 # summarised in profiles/, keyed by workload, kernel and the kernel source's tag
 # (source_tag) at capture time: a kernel changed since its capture reports null
 NCU_TRAFFIC = {
+    # profiles/dmg_kernel_kitti_1242x375x128.md
+    ("kitti", "dmg_kernel horizontal pass", "dae2685973db"): 300_033_280,
+    ("kitti", "dmg_kernel vertical pass", "dae2685973db"): 232_310_272,
     # dram__bytes.sum.per_second x gpu__time_duration.sum of the capture
     ("minorants", "dmm_alt_kernel horizontal pass", "d05e9b6ae61e"): 3_585_900_000,
     ("minorants", "dmm_alt_kernel vertical pass", "d05e9b6ae61e"): 3_333_000_000,
@@ -486,7 +501,13 @@ NCU_TRAFFIC = {
 # bound by instruction issue and latency, so its issue rate is reported beside
 # the HBM roofline, against 152 SMs x 4 schedulers x 1 warp-instruction per
 # cycle at 2070 MHz
-NCU_INSTRUCTIONS = {}
+NCU_INSTRUCTIONS = {
+    ("kitti", "dmg_kernel horizontal pass", "dae2685973db"): 264_086_625,
+    ("kitti", "dmg_kernel vertical pass", "dae2685973db"): 273_201_498,
+}
+# the refinement kernel (profiles/pd_res_kernel_kitti_1242x375x128.md): warp
+# instructions per launch of 100 iterations, keyed by the source tag of pd.cu
+NCU_PD_INSTRUCTIONS = {("pd_res_kernel", 100, "c590292a4644"): 380_328_117}
 ISSUE_PEAK_GINST_S = 152 * 4 * 2.070
 
 
@@ -1321,6 +1342,7 @@ def main():
     roofline["frame_bytes"] = frame_bytes
     roofline["frame_frac"] = round(frame_bytes / (tot_ms / args.steps / 1e3) / 1e9 / peak, 4)
     roofline["stage_ms"] = time_stages(ctx, d_left, d_right, NI, NP, flush, stream)
+    roofline["refinement_kernel"] = refinement_issue(roofline["stage_ms"]["refinement"], NP)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -104,7 +104,7 @@ typedef struct dm_params {
                             /* 2 = uint16                                        */
     int32_t pd_launch;      /* dm_refine: 0 = automatic: all iterations in one   */
                             /* cooperative launch with the state in shared       */
-                            /* memory, one region per SM, where it fits, else 2; */
+                            /* memory, one region per SM, where it fits, else 1; */
                             /* 1 = one launch per iteration; 2 = one cooperative */
                             /* launch, state in global memory, grid barriers.    */
                             /* Same results bit for bit                          */

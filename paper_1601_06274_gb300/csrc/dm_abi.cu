@@ -799,7 +799,7 @@ DM_API int dm_refine(dm_ctx* ctx, int iters, const float* d_u0)
         ctx->have_u = true;
         return DM_OK;
     }
-    if (ctx->p.pd_launch == 0 || ctx->p.pd_launch == 2) {
+    if (ctx->p.pd_launch == 2) {
         // every iteration in one cooperative launch (pd_run_kernel)
         dm::PdRunArgs r{};
         r.set[0] = a;
