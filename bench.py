@@ -981,8 +981,8 @@ def run_minorants(args):
         results[kind] = {"lower_bound_per_iteration": [int(v) for v in lb],
                          "pass_ms": {"horizontal": round(avg[0], 4),
                                      "vertical": round(avg[1], 4)},
-                         "kernel": "dmm16_kernel" if ctx.path()[0] == 16 else
-                                   ("dmm_pass_kernel" if kind == "hier" else "dmm_alt_kernel")}
+                         "kernel": KERNEL_NAMES[ctx.path()[0]] if kind == "hier" else
+                                   "dmm_alt_kernel"}
     # ---- timed region: K solves of 10 iterations with the iterative minorant
     ctx = ctxs["iterative"]
     for _ in range(args.warmup):

@@ -444,8 +444,9 @@ DM_API int dm_batch_discrete_pass(dm_batch* b, int which);
  * caller for d_lam_in (the duals that Dual MM itself produces from such costs
  * stay within it).  Limit: 2 * H * W * KP * 4 bytes <= 32 MiB - 8.25 KiB, where
  * KP is L rounded up to 32, 64, 128 or 256; larger problems return
- * DM_ERR_WORKSPACE before any work is enqueued.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
+ * DM_ERR_WORKSPACE before any work is enqueued.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first
  * call before any stream capture.  All calls share the one array: calls whose
  * work overlaps on the GPU race. */
 DM_API int dm_discrete_pass_noalloc(int H, int W, int L, const dm_params* p, int which,

@@ -371,7 +371,7 @@ def test_gradient_at_200_iterations_matches_oracle_and_central_differences(dm, H
     assert _rel(gc, ogc) <= G_TOL
     assert _rel(ga, oga) <= G_TOL
     assert gl == pytest.approx(ogl, rel=G_TOL, abs=1e-7)
-    # 64 central differences at h = 1e-3 of the FP64 forward (BASELINE's check);
+    # 64 central differences at h = 1e-3 of the FP64 forward;
     # a direction whose quotients at h and h/2 differ straddles a kink
     def lossf(c, a, l):
         uu = O.refine(c, whf, wvf, u064, iters, O.Params(C=C, lambda_r=l, warps=warps), a)[0]
