@@ -713,7 +713,8 @@ def run_batch(args):
     e2e_value = units * args.steps / (sum(e_ms) / 1e3) / 1e6
     peak, src = hbm_peak()
     # ---- dominant kernel: one Dual MM pass over all 32 pairs (the persistent
-    # 16-bit kernel, one launch per group and unit), CUDA events on the batch stream
+    # lane-group kernel, one launch per group and label class), CUDA events on
+    # the batch stream
     pass_ms = {}
     for which in (0, 1):
         evs = []
@@ -728,17 +729,20 @@ def run_batch(args):
         torch.cuda.synchronize()
         pass_ms[which] = sum(x.elapsed_time(y) for x, y in evs) / len(evs)
     pass_bytes = {0: 0, 1: 0}
+    kernels = set()
     for k, (H, W, L) in enumerate(shapes):
-        kern, dbytes = b.pairs[k].path()
-        pb = dmm_pass_bytes(kern, dbytes, 1, H * W, L)
+        kernels.add({8: "dmg_batch_kernel", 16: "dmm16_batch_kernel"}.get(
+            b.pairs[k].path()[0], "dmm_pass_kernel"))
+        pb = survey_pass_bytes(H * W, L)
         pass_bytes[0] += pb[0]
         pass_bytes[1] += pb[1]
     dom = max((0, 1), key=lambda w: pass_ms[w])
     ach = pass_bytes[dom] / (pass_ms[dom] / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(ach, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": None,
-                "kernel": "dmm16_batch_kernel " + ("horizontal" if dom == 0 else "vertical")
+                "kernel": "+".join(sorted(kernels)) + (" horizontal" if dom == 0 else " vertical")
                           + " pass over all pairs", "peak_source": src,
+                "bytes_rule": "5 B (horizontal) / 4 B (vertical) per pixel-label: int16 duals",
                 "bytes_per_launch": pass_bytes[dom],
                 "pass_ms": {"horizontal": round(pass_ms[0], 4), "vertical": round(pass_ms[1], 4)}}
     cpu = None

@@ -314,16 +314,25 @@ dm::Dmm16Args dm16_args(dm_ctx* c, int which)
     return a;
 }
 
-int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
+// arguments of a packed pass on the context's kernel: the lane-group kernel
+// keeps 8-bit messages [chains][n][16 gsz] with the int32 offsets after them
+dm::Dmm16Args pass16_args(dm_ctx* c, int which)
 {
     dm::Dmm16Args a = dm16_args(c, which);
-    a.labels = labels;
-    a.lb = lb;
     if (c->use_g) {
-        // 8-bit messages [chains][n][16 gsz], then the int32 offsets
         const size_t msg = align_up((size_t)c->H * c->W * 16 * c->gsz, 256);
         a.fofs = reinterpret_cast<int32_t*>(c->ws + c->lay.fmsg + msg);
         a.bofs = reinterpret_cast<int32_t*>(c->ws + c->lay.bmsg + msg);
+    }
+    return a;
+}
+
+int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
+{
+    dm::Dmm16Args a = pass16_args(c, which);
+    a.labels = labels;
+    a.lb = lb;
+    if (c->use_g) {
         DM_CK(dm::launch_dmg_pass(a, c->gsz, c->radius, c->delta_bytes, c->stream));
         c->launches += 1;
         return DM_OK;
@@ -417,7 +426,7 @@ int census_cost(dm_ctx* ctx, const uint8_t* d_left, const uint8_t* d_right, bool
 namespace dm {
 namespace ctxops {
 PdArgs pd_args(dm_ctx* c) { return ::pd_args(c); }
-Dmm16Args dm16_args(dm_ctx* c, int which) { return ::dm16_args(c, which); }
+Dmm16Args dm16_args(dm_ctx* c, int which) { return ::pass16_args(c, which); }
 int run_pass(dm_ctx* c, int which, uint16_t* labels, long long* lb)
 {
     return ::run_pass(c, which, labels, lb);

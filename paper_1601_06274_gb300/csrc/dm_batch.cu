@@ -4,10 +4,11 @@
 // Every pair keeps its own dm_ctx (its layout, taps and dual storage) on a
 // slice of one workspace; the batch adds device tables so that the costly
 // steps run as persistent kernels over all pairs at once:
-//   * Dual MM passes: one launch per label class (16-bit kernel instantiation)
-//     and pass; each CTA pulls (pair, chain) tasks, longest chains first, from
-//     a work counter.  Pairs outside the 16-bit kernel's bounds keep their own
-//     launches.
+//   * Dual MM passes: one launch per label class (kernel instantiation: the
+//     lane-group kernel where a pair's bounds admit it, else the one-warp
+//     16-bit kernel) and pass; each CTA pulls (pair, chain) tasks, longest
+//     chains first, from a work counter.  Pairs outside the packed kernels'
+//     bounds keep their own launches.
 //   * primal-dual iterations: one launch per iteration for all pairs; the CTAs
 //     stride over the tiles of every pair (tile shape from the autotuner).
 // Pairs are solved in groups whose working set fits a budget (GB300's L2 holds
@@ -32,7 +33,7 @@
 namespace {
 
 constexpr int kMaxBatchIters = 256;   // Dual MM iterations of one batched solve
-constexpr int kMaxClasses = 12;       // (NP, padded, delta bytes) combinations
+constexpr int kMaxClasses = 24;       // kernel instantiations: (G or NP, padded, delta bytes)
 constexpr int kTuning = 5;            // values of a launch-shape choice
 
 #define DB_CK(call)                                  \
@@ -43,8 +44,10 @@ constexpr int kTuning = 5;            // values of a launch-shape choice
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// a kernel instantiation: the lane-group kernel with g lanes per group, or
+// (g = 0) the one-warp 16-bit kernel with np label pairs per lane
 struct Class {
-    int np = 1, pad = 0, dbytes = 1;
+    int g = 0, np = 1, pad = 0, dbytes = 1;
 };
 
 // one persistent launch: up to kBatchDescs pairs of one class and their tasks
@@ -135,19 +138,20 @@ int prepare(dm_batch* b)
         c->u_cur = c->pq_cur = 0;
         labels[i] = lab;
         if (!c->use16 || !c->discrete_ok) continue;
-        const int pad = c->L != 64 * c->np16 ? 1 : 0;
+        Class want;
+        want.g = c->use_g ? c->gsz : 0;
+        want.np = c->use_g ? 0 : c->np16;
+        want.pad = !c->use_g && c->L != 64 * c->np16 ? 1 : 0;
+        want.dbytes = c->delta_bytes;
         int k = 0;
         for (; k < (int)b->classes.size(); ++k) {
             const Class& q = b->classes[k];
-            if (q.np == c->np16 && q.pad == pad && q.dbytes == c->delta_bytes) break;
+            if (q.g == want.g && q.np == want.np && q.pad == want.pad && q.dbytes == want.dbytes)
+                break;
         }
         if (k == (int)b->classes.size()) {
             if (k == kMaxClasses) return DM_ERR_ARG;
-            Class q;
-            q.np = c->np16;
-            q.pad = pad;
-            q.dbytes = c->delta_bytes;
-            b->classes.push_back(q);
+            b->classes.push_back(want);
         }
         b->cls_of[i] = k;
     }
@@ -262,8 +266,11 @@ int batch_pass(dm_batch* b, const Group& g, int which, int t, bool last)
         a.tasks = reinterpret_cast<const int2*>(b->ws + b->off_tasks) + u.begin;
         a.n_tasks = u.count;
         a.counter = counter;
-        // persistent CTAs: 256 labels (NP = 4) fit two per SM, the others three
-        const int occ = q.np == 4 ? std::min(b->dmm_occ, 2) : b->dmm_occ;
+        // persistent CTAs: for the one-warp kernel 256 labels (NP = 4) fit two
+        // per SM, the others three; the lane-group kernel fits 24 warps per SM
+        // (dmm_occ = 3 takes them all)
+        int occ = q.np == 4 ? std::min(b->dmm_occ, 2) : b->dmm_occ;
+        if (q.g > 0) occ = std::max(1, 8 * b->dmm_occ / std::min(q.g, 8));
         a.grid = std::min(b->sms * occ, u.count);
         a.n_desc = (int)u.pairs.size();
         for (int j = 0; j < a.n_desc; ++j) {
@@ -273,7 +280,11 @@ int batch_pass(dm_batch* b, const Group& g, int which, int t, bool last)
             a.descs[j] = d;
         }
         DB_CK(cudaMemsetAsync(counter, 0, sizeof(int), b->stream));
-        DB_CK(dm::launch_dmm16_batch(a, q.np, b->ctx[0]->radius, q.pad != 0, q.dbytes, b->stream));
+        if (q.g > 0)
+            DB_CK(dm::launch_dmg_batch(a, q.g, b->ctx[0]->radius, q.dbytes, b->stream));
+        else
+            DB_CK(dm::launch_dmm16_batch(a, q.np, b->ctx[0]->radius, q.pad != 0, q.dbytes,
+                                         b->stream));
         b->launches += 1;
     }
     for (int i = g.first; i < g.first + g.n; ++i) {
@@ -331,7 +342,8 @@ int batch_solve(dm_batch* b, const uint8_t* const* d_left, const uint8_t* const*
         const unsigned long long before = c->launches;
         if ((rc = dm_cost_volume(c, d_left[i], d_right[i]))) return rc;
         b->launches += c->launches - before;
-        if ((c->use16 && c->discrete_ok) != (b->cls_of[i] >= 0))
+        if ((c->use16 && c->discrete_ok) != (b->cls_of[i] >= 0) ||
+            (b->cls_of[i] >= 0 && b->classes[b->cls_of[i]].g != (c->use_g ? c->gsz : 0)))
             return DM_ERR_STATE;  // the plan no longer matches the pair's kernel
         DB_CK(cudaMemsetAsync(c->ws + c->lay.lb, 0, dmm_iters * sizeof(long long), b->stream));
     }

@@ -3,4 +3,5 @@
 
 namespace dm {
 template cudaError_t launch_g<1, int16_t>(const Dmm16Args&, int, cudaStream_t);
+template cudaError_t launch_g_batch<1, int16_t>(const Batch16Args&, int, cudaStream_t);
 }  // namespace dm

@@ -1273,6 +1273,36 @@ __global__ void __launch_bounds__(warps_of<LP / 16>() * 32, 24 / warps_of<LP / 1
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Persistent form over the chains of many pairs of one label class (the
+// batched solve): every CTA takes (pair, chain) tasks from a work counter,
+// longest chains first, until none are left.  All pairs share the penalty (one
+// taps table).  A chain's work is chain_g's, exactly as in dmg_kernel.
+template <int LP, int R, typename DT>
+__global__ void __launch_bounds__(warps_of<LP / 16>() * 32, 24 / warps_of<LP / 16>())
+    dmg_batch_kernel(const __grid_constant__ Batch16Args B)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ int s_t;
+    uint32_t* s_taps = reinterpret_cast<uint32_t*>(smem);
+    constexpr int TW = tap_words<R>();
+    const uint32_t* taps = B.descs[0].taps16;
+    for (int t = threadIdx.x; t < 256 * TW; t += blockDim.x) s_taps[t] = taps[(t / TW) * kTapW + t % TW];
+    Dmm16Args* s_args = reinterpret_cast<Dmm16Args*>(smem + smem_g<LP, R, DT>() -
+                                                     ((sizeof(Dmm16Args) + 15) & ~(size_t)15));
+#pragma unroll 1
+    for (;;) {
+        if (threadIdx.x == 0) s_t = atomicAdd(B.counter, 1);
+        __syncthreads();
+        const int t = s_t;
+        if (t >= B.n_tasks) break;
+        const int2 tk = B.tasks[t];
+        if (threadIdx.x == 0) *s_args = B.descs[tk.x];
+        __syncthreads();
+        chain_g<LP, DT, R>(B.descs[tk.x], s_args, tk.y, smem, s_taps);
+        __syncthreads();
+    }
+}
+
 constexpr int kMaxDevices = 64;
 
 template <typename K>
@@ -1309,6 +1339,17 @@ cudaError_t launch_one(const Dmm16Args& a, cudaStream_t s)
     return cudaLaunchKernelEx(&cfg, dmg_kernel<LP, R, DT>, a);
 }
 
+template <int LP, int R, typename DT>
+cudaError_t launch_batch_one(const Batch16Args& b, cudaStream_t s)
+{
+    const int smem = smem_g<LP, R, DT>();
+    static std::atomic<int> done[kMaxDevices];
+    const cudaError_t e = ensure_smem(dmg_batch_kernel<LP, R, DT>, smem, done);
+    if (e != cudaSuccess) return e;
+    dmg_batch_kernel<LP, R, DT><<<b.grid, warps_of<LP / 16>() * 32, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
 }  // namespace kg
 
 // Launcher of one label class (G lanes of 16 labels per group in the group
@@ -1320,6 +1361,16 @@ cudaError_t launch_g(const Dmm16Args& a, int radius, cudaStream_t s)
         case 1: return kg::launch_one<16 * G, 1, DT>(a, s);
         case 2: return kg::launch_one<16 * G, 2, DT>(a, s);
         default: return kg::launch_one<16 * G, 4, DT>(a, s);
+    }
+}
+
+template <int G, typename DT>
+cudaError_t launch_g_batch(const Batch16Args& b, int radius, cudaStream_t s)
+{
+    switch (radius) {
+        case 1: return kg::launch_batch_one<16 * G, 1, DT>(b, s);
+        case 2: return kg::launch_batch_one<16 * G, 2, DT>(b, s);
+        default: return kg::launch_batch_one<16 * G, 4, DT>(b, s);
     }
 }
 

@@ -15,6 +15,8 @@ template <int NP, typename DT>
 cudaError_t launch16_batch(const Batch16Args& b, int radius, bool pad, cudaStream_t s);
 template <int G, typename DT>
 cudaError_t launch_g(const Dmm16Args& a, int radius, cudaStream_t s);
+template <int G, typename DT>
+cudaError_t launch_g_batch(const Batch16Args& b, int radius, cudaStream_t s);
 
 namespace {
 
@@ -131,6 +133,26 @@ cudaError_t launch_dmg_pass(const Dmm16Args& a, int g, int radius, int delta_byt
         case 4: return launch_g<4, int16_t>(a, radius, s);
         case 8: return launch_g<8, int16_t>(a, radius, s);
         default: return launch_g<16, int16_t>(a, radius, s);
+    }
+}
+
+cudaError_t launch_dmg_batch(const Batch16Args& b, int g, int radius, int delta_bytes, cudaStream_t s)
+{
+    if (delta_bytes == 1) {
+        switch (g) {
+            case 1: return launch_g_batch<1, uint8_t>(b, radius, s);
+            case 2: return launch_g_batch<2, uint8_t>(b, radius, s);
+            case 4: return launch_g_batch<4, uint8_t>(b, radius, s);
+            case 8: return launch_g_batch<8, uint8_t>(b, radius, s);
+            default: return launch_g_batch<16, uint8_t>(b, radius, s);
+        }
+    }
+    switch (g) {
+        case 1: return launch_g_batch<1, int16_t>(b, radius, s);
+        case 2: return launch_g_batch<2, int16_t>(b, radius, s);
+        case 4: return launch_g_batch<4, int16_t>(b, radius, s);
+        case 8: return launch_g_batch<8, int16_t>(b, radius, s);
+        default: return launch_g_batch<16, int16_t>(b, radius, s);
     }
 }
 
