@@ -1104,7 +1104,7 @@ __device__ __noinline__ void leaf_call(const Dmm16Args* A, const uint32_t* s_tap
 // segments know which ones exist.  In the depth-first part a warp decides by the
 // longest segment among its own groups, which keeps its subtrees consistent
 // because no other warp touches them.
-template <int LP, typename DT, int R>
+template <int LP, typename DT, int R, int NW = warps_of<LP / 16>()>
 __device__ __forceinline__ void chain_g(const Dmm16Args& A, const Dmm16Args* s_args, int chain, uint8_t* smem,
                                         const uint32_t* s_taps)
 {
@@ -1118,7 +1118,7 @@ __device__ __forceinline__ void chain_g(const Dmm16Args& A, const Dmm16Args* s_a
     // the whole-warp ring fits in front of the last area's message slots
     static_assert(!WIDE || RB * Geo<YW>::BLK <= ROOM, "whole-warp staging ring");
     using Ar = Area<LP, DT>;
-    constexpr int NWARP = warps_of<GD>();
+    constexpr int NWARP = NW;
     constexpr int NG = NWARP * 32 / GD;         // groups per CTA
     constexpr int KL = NG >= 32 ? 5 : (NG >= 16 ? 4 : (NG >= 8 ? 3 : 2));  // log2(NG)
     static_assert((1 << KL) == NG, "groups per CTA must be a power of two");
@@ -1244,10 +1244,10 @@ __device__ __forceinline__ void chain_g(const Dmm16Args& A, const Dmm16Args* s_a
         atomicAdd(reinterpret_cast<unsigned long long*>(A.lb), (unsigned long long)*s_lb);
 }
 
-template <int LP, int R, typename DT>
+template <int LP, int R, typename DT, int NW = warps_of<LP / 16>()>
 constexpr int smem_g()
 {
-    constexpr int NG = warps_of<LP / 16>() * 32 / (LP / 16);
+    constexpr int NG = NW * 32 / (LP / 16);
     return 256 * tap_words<R>() * 4 + NG * (Area<LP, DT>::GRP + kStack * 4 + 8) +
            (int)((sizeof(Dmm16Args) + 15) & ~(size_t)15);
 }
@@ -1255,21 +1255,20 @@ constexpr int smem_g()
 // Launched with programmatic stream serialisation: the taps table (which no
 // pass writes) is staged while the previous pass drains; everything else waits
 // for that grid (griddepcontrol.wait).  Without the attribute both are no-ops.
-template <int LP, int R, typename DT>
-__global__ void __launch_bounds__(warps_of<LP / 16>() * 32, 24 / warps_of<LP / 16>())
-    dmg_kernel(const Dmm16Args A)
+template <int LP, int R, typename DT, int NW = warps_of<LP / 16>()>
+__global__ void __launch_bounds__(NW * 32, 24 / NW) dmg_kernel(const Dmm16Args A)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t* s_taps = reinterpret_cast<uint32_t*>(smem);
     constexpr int TW = tap_words<R>();
     for (int t = threadIdx.x; t < 256 * TW; t += blockDim.x) s_taps[t] = A.taps16[(t / TW) * kTapW + t % TW];
     // the arguments, for the leaf blocks' calls, at the end of the dynamic shared memory
-    Dmm16Args* s_args = reinterpret_cast<Dmm16Args*>(smem + smem_g<LP, R, DT>() -
+    Dmm16Args* s_args = reinterpret_cast<Dmm16Args*>(smem + smem_g<LP, R, DT, NW>() -
                                                      ((sizeof(Dmm16Args) + 15) & ~(size_t)15));
     if (threadIdx.x == 0) *s_args = A;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     __syncthreads();
-    chain_g<LP, DT, R>(A, s_args, blockIdx.x, smem, s_taps);
+    chain_g<LP, DT, R, NW>(A, s_args, blockIdx.x, smem, s_taps);
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
@@ -1318,17 +1317,17 @@ cudaError_t ensure_smem(K kernel, int smem, std::atomic<int> (&done)[kMaxDevices
     return e;
 }
 
-template <int LP, int R, typename DT>
+template <int LP, int R, typename DT, int NW = warps_of<LP / 16>()>
 cudaError_t launch_one(const Dmm16Args& a, cudaStream_t s)
 {
-    const int smem = smem_g<LP, R, DT>();
+    const int smem = smem_g<LP, R, DT, NW>();
     static std::atomic<int> done[kMaxDevices];
-    const cudaError_t e = ensure_smem(dmg_kernel<LP, R, DT>, smem, done);
+    const cudaError_t e = ensure_smem(dmg_kernel<LP, R, DT, NW>, smem, done);
     if (e != cudaSuccess) return e;
     const int chains = a.which == 0 ? a.H : a.W;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(chains);
-    cfg.blockDim = dim3(warps_of<LP / 16>() * 32);
+    cfg.blockDim = dim3(NW * 32);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -1336,7 +1335,7 @@ cudaError_t launch_one(const Dmm16Args& a, cudaStream_t s)
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, dmg_kernel<LP, R, DT>, a);
+    return cudaLaunchKernelEx(&cfg, dmg_kernel<LP, R, DT, NW>, a);
 }
 
 template <int LP, int R, typename DT>
@@ -1354,9 +1353,23 @@ cudaError_t launch_batch_one(const Batch16Args& b, cudaStream_t s)
 
 // Launcher of one label class (G lanes of 16 labels per group in the group
 // layout); each is instantiated in its own translation unit.
+// The vertical pass at 128 labels (1242 chains of 375 nodes on the benchmark
+// frame) runs CTAs of 4 warps: five fit on an SM, so the chains take 1.6 waves
+// instead of 2.7, and more top levels (latency-bound) overlap per SM.  Measured
+// per pass at 1242x375x128: 0.399 ms with 4 warps against 0.425 (8) and 0.432
+// (2); the horizontal pass is fastest with 8.
 template <int G, typename DT>
 cudaError_t launch_g(const Dmm16Args& a, int radius, cudaStream_t s)
 {
+    if constexpr (G == 8) {
+        if (a.which == 1) {
+            switch (radius) {
+                case 1: return kg::launch_one<16 * G, 1, DT, 4>(a, s);
+                case 2: return kg::launch_one<16 * G, 2, DT, 4>(a, s);
+                default: return kg::launch_one<16 * G, 4, DT, 4>(a, s);
+            }
+        }
+    }
     switch (radius) {
         case 1: return kg::launch_one<16 * G, 1, DT>(a, s);
         case 2: return kg::launch_one<16 * G, 2, DT>(a, s);
