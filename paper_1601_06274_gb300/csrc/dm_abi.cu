@@ -89,6 +89,7 @@ bool params_ok(const dm_params& p)
         return false;
     if (p.warps < 1) return false;
     if (p.cost_bytes < 0 || p.cost_bytes > 2) return false;
+    if (p.dmm_path < 0 || p.dmm_path > 3) return false;
     if (p.pd_launch < 0 || p.pd_launch > 2 || p.wait_test < 0) return false;
     return true;
 }
@@ -247,6 +248,9 @@ struct Range {
     ~Range() { nvtxRangePop(); }
 };
 
+// the split Dual MM pass's counters
+size_t pool_bytes(const dm_ctx*) { return dm::kPoolHead * sizeof(int32_t); }
+
 int check_device_error(dm_ctx* c)
 {
     int32_t err = 0;
@@ -261,6 +265,7 @@ int check_device_error(dm_ctx* c)
         // cleared once reported: the barriers of the next one-launch
         // refinement give up as soon as they see it
         DM_CK(cudaMemsetAsync(c->ws + c->lay.err, 0, sizeof(int32_t), c->stream));
+        DM_CK(cudaMemsetAsync(c->ws + c->lay.pool, 0, pool_bytes(c), c->stream));
         DM_CK(cudaStreamSynchronize(c->stream));
         return DM_ERR_TIMEOUT;
     }
@@ -333,6 +338,7 @@ int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
     a.labels = labels;
     a.lb = lb;
     if (c->use_g) {
+        if (c->pool_g) a.pool = reinterpret_cast<int32_t*>(c->ws + c->lay.pool);
         DM_CK(dm::launch_dmg_pass(a, c->gsz, c->radius, c->delta_bytes, c->stream));
         c->launches += 1;
         return DM_OK;
@@ -512,9 +518,10 @@ DM_API int dm_create(int H, int W, int L, const dm_params* p, dm_ctx** out)
     }
     // the 16-bit kernel stages each unary row as four async copies of L/4 bytes
     // (uint8 deltas) or L/2 bytes (int16), so L must be a multiple of 16
-    c->can16 = c->discrete_ok && (p->dmm_path == 0 || p->dmm_path == 2) && (L % 16) == 0 &&
-               c->p2_all <= 8000 && H <= 8192 && W <= 8192;
-    c->can_g = c->can16 && p->dmm_path == 0;
+    c->can16 = c->discrete_ok && p->dmm_path != 1 && (L % 16) == 0 && c->p2_all <= 8000 &&
+               H <= 8192 && W <= 8192;
+    c->can_g = c->can16 && p->dmm_path != 2;
+    c->pool_g = p->dmm_path == 0;
     c->gsz = L <= 16 ? 1 : (L <= 32 ? 2 : (L <= 64 ? 4 : (L <= 128 ? 8 : 16)));
     // workspace layout
     dm::Layout& l = c->lay;
@@ -560,6 +567,7 @@ DM_API int dm_create(int H, int W, int L, const dm_params* p, dm_ctx** out)
     l.epart = add(1024 * sizeof(double));
     l.err = add(sizeof(int32_t));
     l.bar = add(sizeof(uint32_t));
+    l.pool = add(pool_bytes(c));
     l.total = align_up(tot, 256);
     *out = c;
     return DM_OK;
@@ -601,6 +609,7 @@ DM_API int dm_bind_workspace(dm_ctx* ctx, void* d_workspace, size_t bytes)
                           ctx->taps16.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
                           ctx->stream));
     DM_CK(cudaMemsetAsync(ctx->ws + ctx->lay.err, 0, sizeof(int32_t), ctx->stream));
+    DM_CK(cudaMemsetAsync(ctx->ws + ctx->lay.pool, 0, pool_bytes(ctx), ctx->stream));
     DM_CK(cudaStreamSynchronize(ctx->stream));
     return DM_OK;
 }

@@ -19,6 +19,7 @@ struct dm_ctx {
     // every penalty cap fits its 8-bit messages; gsz lanes of 16 labels per message
     bool can_g = false;
     bool use_g = false;
+    bool pool_g = true;         // the lane-group pass may run split (dmg_units_kernel)
     int gsz = 8;
     int delta_bytes = 2;
     int p2_all = 0;             // largest cap omega*C over every usable omega

@@ -30,7 +30,7 @@ constexpr int kDevErrTimeout = 8;  // a bounded device-side wait gave up
 
 struct Layout {
     size_t cost, census, img, wh, wv, lam_h, lam_v, fmsg, bmsg, labels, lb, taps, taps16;
-    size_t u, u_new, u0, s1, s2, lo, hi, ph, pv, qh, qv, ph2, pv2, qh2, qv2, epart, err, bar;
+    size_t u, u_new, u0, s1, s2, lo, hi, ph, pv, qh, qv, ph2, pv2, qh2, qv2, epart, err, bar, pool;
     size_t total;
 };
 
@@ -77,7 +77,11 @@ struct Dmm16Args {
     uint16_t* labels;
     long long* lb;
     int seg_cap;             // entries of each segment-start array: 2^ceil(log2 n) + 1, padded
+    // nullable: the counters of the split lane-group pass ([0] units taken,
+    // [1] CTAs done); zero at launch and again after it
+    int32_t* pool;
 };
+constexpr int kPoolHead = 8;   // ints of a pool
 
 // Persistent batched form of the 16-bit pass over the chains of up to
 // kBatchDescs pairs of one label class (dmm16_impl.cuh).  The descriptors travel

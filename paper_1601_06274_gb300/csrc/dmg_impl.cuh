@@ -38,6 +38,7 @@
 
 #pragma once
 
+#include <algorithm>
 #include <atomic>
 #include <climits>
 
@@ -1104,9 +1105,16 @@ __device__ __noinline__ void leaf_call(const Dmm16Args* A, const uint32_t* s_tap
 // segments know which ones exist.  In the depth-first part a warp decides by the
 // longest segment among its own groups, which keeps its subtrees consistent
 // because no other warp touches them.
+//
+// phase 0 runs the whole chain (every thread of the CTA).  The pooled pass
+// splits it: phase 1 (every thread) runs the levels down to KL, one level
+// further than phase 0's level-synchronous part, and stops; phase 2 (one warp)
+// walks the depth-first subtrees of that warp's groups from the level-(KL+1)
+// segments seg0, seg0 + 1, ... of the chain, reading everything it needs from
+// memory, with no CTA barrier.
 template <int LP, typename DT, int R, int NW = warps_of<LP / 16>()>
 __device__ __forceinline__ void chain_g(const Dmm16Args& A, const Dmm16Args* s_args, int chain, uint8_t* smem,
-                                        const uint32_t* s_taps)
+                                        const uint32_t* s_taps, int phase = 0, int seg0 = 0)
 {
     constexpr int GD = LP / 16;                 // lanes per group of the group layout
     constexpr bool WIDE = LP >= 64;             // a warp holds a message with >= 2 labels per lane
@@ -1131,19 +1139,34 @@ __device__ __forceinline__ void chain_g(const Dmm16Args& A, const Dmm16Args* s_a
     uint32_t* s_stk = reinterpret_cast<uint32_t*>(gtail) + gd * kStack;
     long long* s_lb = reinterpret_cast<long long*>(gtail + NG * kStack * 4) + gd;
     if (qd == 0) *s_lb = 0;
-    // zero boundary messages at both chain ends
-    if (threadIdx.x < 32) {
-        const Lane<YW> lw = make_lane<YW>(A, areas, GD);
-        Msg<YW::NWL> zero;
-        zero_msg(zero);
-        store_msg<YW>(reinterpret_cast<uint8_t*>(A.fmsg), A.fofs, C, 0, lw, zero, lw.g == 0);
-        store_msg<YW>(reinterpret_cast<uint8_t*>(A.bmsg), A.bofs, C, n - 1, lw, zero, lw.g == 0);
-    }
-    __syncthreads();
     const int warp = (int)threadIdx.x >> 5;
     int round = 0;   // 0, 1: the root; then level = round - 1
     bool dfs = false;
     int sp = 0;      // depth-first stack size (warp-uniform)
+    // the first level walked depth first: KL, or KL + 1 in the pooled pass
+    const int LD = phase == 0 ? KL : KL + 1;
+    if (phase != 2) {
+        // zero boundary messages at both chain ends
+        if (threadIdx.x < 32) {
+            const Lane<YW> lw = make_lane<YW>(A, areas, GD);
+            Msg<YW::NWL> zero;
+            zero_msg(zero);
+            store_msg<YW>(reinterpret_cast<uint8_t*>(A.fmsg), A.fofs, C, 0, lw, zero, lw.g == 0);
+            store_msg<YW>(reinterpret_cast<uint8_t*>(A.bmsg), A.bofs, C, n - 1, lw, zero, lw.g == 0);
+        }
+        __syncthreads();
+    } else {
+        // this warp's groups take the level-LD segments seg0 + (their index in the warp)
+        dfs = true;
+        const int s = seg0 + gd % (32 / GD);
+        int a = 0, b = 0;
+        const int l = segment_of(n, LD, s, a, b);
+        if (qd == 0)
+            s_stk[0] = (uint32_t)(l > 0 ? a : 0) | ((uint32_t)(l > 0 ? b : 0) << 15) |
+                       ((uint32_t)(s & 1) << 30) | (l > 0 ? 0x80000000u : 0u);
+        sp = 1;
+        __syncwarp();
+    }
     int rounds = 0;  // bounded: at most KL + 2 level rounds and 2n depth-first steps
 #pragma unroll 1
     for (;;) {
@@ -1172,7 +1195,7 @@ __device__ __forceinline__ void chain_g(const Dmm16Args& A, const Dmm16Args* s_a
                     b = len > 0 ? n - 1 : 0;
                     type = me == 0 ? 1 : 0;  // forward half, backward half
                 }
-            } else if (level < KL && level_max(n, level - 1) >= 5) {
+            } else if (level < LD && level_max(n, level - 1) >= 5) {
                 const int nseg = 1 << level;
                 if (nseg <= NWIDE && level_max(n, level) >= 5) {
                     // whole-warp layout (or the group layout when LP < 64)
@@ -1191,7 +1214,9 @@ __device__ __forceinline__ void chain_g(const Dmm16Args& A, const Dmm16Args* s_a
                     maxlen = __reduce_max_sync(kFull, len);
                 }
             } else {
-                // from level KL on every group walks its segment's subtree depth first
+                // from level KL on every group walks its segment's subtree depth
+                // first (in the pooled pass, from level KL + 1, in phase 2)
+                if (phase == 1) break;
                 dfs = true;
                 if (level == KL && level_max(n, KL - 1) >= 5) {
                     const int l = segment_of(n, KL, gd, a, b);
@@ -1255,7 +1280,7 @@ constexpr int smem_g()
 // Launched with programmatic stream serialisation: the taps table (which no
 // pass writes) is staged while the previous pass drains; everything else waits
 // for that grid (griddepcontrol.wait).  Without the attribute both are no-ops.
-template <int LP, int R, typename DT, int NW = warps_of<LP / 16>()>
+template <int LP, int R, typename DT, int NW = warps_of<LP / 16>(), int PH = 0>
 __global__ void __launch_bounds__(NW * 32, 24 / NW) dmg_kernel(const Dmm16Args A)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -1268,7 +1293,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW) dmg_kernel(const Dmm16Args A
     if (threadIdx.x == 0) *s_args = A;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     __syncthreads();
-    chain_g<LP, DT, R, NW>(A, s_args, blockIdx.x, smem, s_taps);
+    chain_g<LP, DT, R, NW>(A, s_args, blockIdx.x, smem, s_taps, PH);
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
@@ -1300,6 +1325,54 @@ __global__ void __launch_bounds__(warps_of<LP / 16>() * 32, 24 / warps_of<LP / 1
         chain_g<LP, DT, R>(B.descs[tk.x], s_args, tk.y, smem, s_taps);
         __syncthreads();
     }
+}
+
+// The split pass, for chains whose depth-first part would leave some SMs
+// idle: dmg_kernel<..., 1> runs every chain's levels down to KL (chain_g phase
+// 1, one CTA per chain), then this kernel (launched after it; its
+// griddepcontrol.wait waits for that grid and its memory) shares the
+// depth-first part, cut into 2 NW units per chain (the level-(KL+1) segments of
+// one warp's groups each), among persistent CTAs: every warp takes units from
+// one counter (pool[0]) until none is left.  The last CTA out zeroes the
+// counters (pool[0], pool[1]) for the next launch.  Results equal dmg_kernel's
+// bit for bit.
+template <int LP, int R, typename DT, int NW = warps_of<LP / 16>()>
+__global__ void __launch_bounds__(NW * 32, 24 / NW) dmg_units_kernel(const Dmm16Args A)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ int s_last;
+    constexpr int GD = LP / 16, GPW = 32 / GD, NU = 2 * NW;
+    uint32_t* s_taps = reinterpret_cast<uint32_t*>(smem);
+    constexpr int TW = tap_words<R>();
+    for (int t = threadIdx.x; t < 256 * TW; t += blockDim.x) s_taps[t] = A.taps16[(t / TW) * kTapW + t % TW];
+    Dmm16Args* s_args = reinterpret_cast<Dmm16Args*>(smem + smem_g<LP, R, DT, NW>() -
+                                                     ((sizeof(Dmm16Args) + 15) & ~(size_t)15));
+    if (threadIdx.x == 0) *s_args = A;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    __syncthreads();
+    int* const P = A.pool;
+    const int chains = A.which == 0 ? A.H : A.W;
+    const int units = chains * NU;
+    const int lane = (int)threadIdx.x & 31;
+#pragma unroll 1
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(P, 1);
+        u = __shfl_sync(kFull, u, 0);
+        if (u >= units) break;
+        chain_g<LP, DT, R, NW>(A, s_args, u / NU, smem, s_taps, 2, (u % NU) * GPW);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(P + 1, 1) == (int)gridDim.x - 1;
+        if (s_last) {
+            P[0] = 0;
+            __threadfence();
+            P[1] = 0;
+        }
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 constexpr int kMaxDevices = 64;
@@ -1338,6 +1411,56 @@ cudaError_t launch_one(const Dmm16Args& a, cudaStream_t s)
     return cudaLaunchKernelEx(&cfg, dmg_kernel<LP, R, DT, NW>, a);
 }
 
+// the split pass: the levels down to KL with one CTA per chain, then the
+// depth-first units on as many persistent CTAs as fit at once
+template <int LP, int R, typename DT, int NW = warps_of<LP / 16>()>
+cudaError_t launch_split(const Dmm16Args& a, cudaStream_t s)
+{
+    const int smem = smem_g<LP, R, DT, NW>();
+    static std::atomic<int> done_t[kMaxDevices], done_u[kMaxDevices];
+    cudaError_t e = ensure_smem(dmg_kernel<LP, R, DT, NW, 1>, smem, done_t);
+    if (e == cudaSuccess) e = ensure_smem(dmg_units_kernel<LP, R, DT, NW>, smem, done_u);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dmg_units_kernel<LP, R, DT, NW>,
+                                                          NW * 32, smem);
+    if (e != cudaSuccess) return e;
+    const int chains = a.which == 0 ? a.H : a.W;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(NW * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(chains);
+    e = cudaLaunchKernelEx(&cfg, dmg_kernel<LP, R, DT, NW, 1>, a);
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3(std::max(1, std::min(chains * 2 * NW, sms * per_sm)));
+    return cudaLaunchKernelEx(&cfg, dmg_units_kernel<LP, R, DT, NW>, a);
+}
+
+// one pass: split when a.pool is set (and the chains have units), else one
+// CTA per chain.  Measured at 1242x375x128: the horizontal pass (375 chains for
+// 456 CTA slots) takes 0.448 ms split against 0.467 ms; the vertical pass gains
+// nothing (0.384 ms either way) and stays one CTA per chain; units cut at level
+// KL rather than KL + 1 made the horizontal pass slower (0.483 ms).
+template <int LP, int R, typename DT, int NW = warps_of<LP / 16>()>
+cudaError_t launch_pass(const Dmm16Args& a, cudaStream_t s)
+{
+    constexpr int NG = NW * (32 / (LP / 16));
+    constexpr int KL = NG >= 32 ? 5 : (NG >= 16 ? 4 : (NG >= 8 ? 3 : 2));
+    const int n = a.which == 0 ? a.W : a.H;
+    const bool units = n > 4 && ((n + (1 << KL) - 1) >> KL) >= 5;
+    return a.pool != nullptr && units ? launch_split<LP, R, DT, NW>(a, s)
+                                      : launch_one<LP, R, DT, NW>(a, s);
+}
+
 template <int LP, int R, typename DT>
 cudaError_t launch_batch_one(const Batch16Args& b, cudaStream_t s)
 {
@@ -1371,9 +1494,9 @@ cudaError_t launch_g(const Dmm16Args& a, int radius, cudaStream_t s)
         }
     }
     switch (radius) {
-        case 1: return kg::launch_one<16 * G, 1, DT>(a, s);
-        case 2: return kg::launch_one<16 * G, 2, DT>(a, s);
-        default: return kg::launch_one<16 * G, 4, DT>(a, s);
+        case 1: return kg::launch_pass<16 * G, 1, DT>(a, s);
+        case 2: return kg::launch_pass<16 * G, 2, DT>(a, s);
+        default: return kg::launch_pass<16 * G, 4, DT>(a, s);
     }
 }
 

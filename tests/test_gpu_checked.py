@@ -41,11 +41,11 @@ def passes(ctx, cost, wh, wv, iters):
 
 for (H, W, L) in [(1, 37, 16), (23, 1, 16), (2, 3, 16), (5, 6, 32), (13, 29, 48), (9, 21, 64),
                   (7, 19, 128), (4, 9, 256), (3, 1000, 16), (600, 2, 32), (5, 777, 128), (300, 3, 256)]:
-    for cb, path in ((1, 0), (2, 0), (1, 2), (2, 2)):
+    for cb, path in ((1, 0), (2, 0), (1, 2), (2, 2), (1, 3)):
         sp = S.make_pair(H, W, L, planes=3, noise_sigma=2.0, seed=H * W + L)
         ctx = dm.Context(H, W, L, dm.default_params(cost_bytes=cb, dmm_path=path))
         ctx.cost_volume(sp.left, sp.right)
-        assert ctx.path()[0] == (8 if path == 0 else 16)
+        assert ctx.path()[0] == (16 if path == 2 else 8)
         cost = O.cost_volume(sp.left, sp.right, L)
         wh, wv = O.edge_weights(sp.left)
         passes(ctx, cost, wh, wv, 2)

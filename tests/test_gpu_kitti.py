@@ -56,7 +56,7 @@ def test_inputs_match_the_stored_frame(setup):
     assert _sha(sp.left) == g["left_sha256"] and _sha(sp.right) == g["right_sha256"]
 
 
-@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("path", [0, 1, 2, 3])
 def test_full_frame_discrete_bit_exact(setup, path):
     dm, g, sp = setup
     H, W, L = g["H"], g["W"], g["L"]

@@ -87,7 +87,7 @@ def _check_passes(dm, ctx, cost, wh, wv, iters, P):
 
 
 @pytest.mark.parametrize("H,W,L", SHAPES)
-@pytest.mark.parametrize("path", [0, 1, 2])  # lane groups / int32 / one warp per chain
+@pytest.mark.parametrize("path", [0, 1, 2, 3])  # lane groups pooled / int32 / one warp per chain / lane groups per chain
 def test_dmm_passes_bit_exact(dm, H, W, L, path):
     left, right = _pair(H, W, L, seed=7 * H + W + L)
     ctx = _ctx(dm, H, W, L, dmm_path=path)
@@ -111,7 +111,7 @@ def test_dmm_passes_with_more_chains_than_one_round(dm, H, W, L):
 
 
 @pytest.mark.parametrize("H,W,L", [(9, 14, 16), (5, 40, 64), (12, 8, 128), (3, 5, 200)])
-@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("path", [0, 1, 2, 3])
 def test_dmm_passes_extreme_costs_and_weights(dm, H, W, L, path):
     # full uint8 cost range and every usable omega (multiples of 4 up to 252)
     rng = np.random.default_rng(H * W * L)
@@ -143,7 +143,7 @@ def test_dmm_other_penalties(dm, params):
 
 @pytest.mark.parametrize("H,W,L,iters", [(48, 64, 16, 5), (17, 31, 48, 4), (1, 50, 12, 2),
                                          (40, 1, 12, 2), (30, 70, 128, 3)])
-@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("path", [0, 1, 2, 3])
 def test_discrete_labels_and_bounds(dm, H, W, L, iters, path):
     left, right = _pair(H, W, L, seed=H + W)
     ctx = _ctx(dm, H, W, L, dmm_path=path)
@@ -160,7 +160,7 @@ def test_discrete_labels_and_bounds(dm, H, W, L, iters, path):
 
 
 @pytest.mark.parametrize("H,W,L", [(7, 9, 16), (5, 33, 64), (9, 6, 128)])
-@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("path", [0, 1, 2, 3])
 def test_all_equal_costs_break_ties_to_the_smallest_label(dm, H, W, L, path):
     cost = np.full((H, W, L), 7, dtype=np.uint8)
     wh = np.full((H, W), 8, dtype=np.uint8)
