@@ -1493,10 +1493,19 @@ cudaError_t launch_g(const Dmm16Args& a, int radius, cudaStream_t s)
             }
         }
     }
+    // the split pass from 128 labels on (at 64 labels, the two concurrent layers
+    // of optical flow lost 3 % to it)
+    if constexpr (G >= 8) {
+        switch (radius) {
+            case 1: return kg::launch_pass<16 * G, 1, DT>(a, s);
+            case 2: return kg::launch_pass<16 * G, 2, DT>(a, s);
+            default: return kg::launch_pass<16 * G, 4, DT>(a, s);
+        }
+    }
     switch (radius) {
-        case 1: return kg::launch_pass<16 * G, 1, DT>(a, s);
-        case 2: return kg::launch_pass<16 * G, 2, DT>(a, s);
-        default: return kg::launch_pass<16 * G, 4, DT>(a, s);
+        case 1: return kg::launch_one<16 * G, 1, DT>(a, s);
+        case 2: return kg::launch_one<16 * G, 2, DT>(a, s);
+        default: return kg::launch_one<16 * G, 4, DT>(a, s);
     }
 }
 
