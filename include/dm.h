@@ -97,8 +97,9 @@ typedef struct dm_params {
     int32_t dmm_path;       /* Dual MM kernel: 0 = automatic (packed 16-bit     */
                             /* arithmetic on lane groups with 8-bit messages     */
                             /* whenever its value bounds hold; from 128 labels   */
-                            /* on, the horizontal pass's depth-first work shared */
-                            /* by persistent CTAs;                               */
+                            /* on, a pass's depth-first work is shared by        */
+                            /* persistent CTAs (at 128 labels, the horizontal    */
+                            /* pass's only);                                     */
                             /* else one warp per chain, else int32), 1 = always  */
                             /* the int32 kernel, 2 = packed one-warp-per-chain   */
                             /* kernel where its bounds hold, else int32, 3 = as  */
