@@ -465,6 +465,10 @@ def roofline_line(ctx, avg, HW, L, cost_bytes, kernel_names, workload="kitti"):
     sec = avg[dom] / 1e3
     achieved = alg[dom] / sec / 1e9
     name = kernel_names[kernel] + (" horizontal" if dom == 0 else " vertical") + " pass"
+    # from 128 labels on, a lane-group pass runs as two kernels: the top levels
+    # (one CTA per chain), then the depth-first units on persistent CTAs; the
+    # vertical pass at 128 labels stays one kernel
+    split = kernel == 8 and L >= 128 and not (L <= 128 and dom == 1)
     key = (workload, name, source_tag(KERNEL_FILES[kernel]))
     line = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC.get(key),
@@ -474,6 +478,9 @@ def roofline_line(ctx, avg, HW, L, cost_bytes, kernel_names, workload="kitti"):
             "storage_bytes_per_launch": own[dom],
             "dual_storage": f"{dbytes}-byte deltas" if kernel in (8, 16) else "int32",
             "pass_ms": {"horizontal": round(avg[0], 4), "vertical": round(avg[1], 4)}}
+    if split:
+        line["kernels"] = ["dmg_kernel (levels down to KL, one CTA per chain)",
+                           "dmg_units_kernel (depth-first units, persistent CTAs)"]
     inst = NCU_INSTRUCTIONS.get(key)
     if inst is not None:
         rate = inst / sec / 1e9
