@@ -496,9 +496,10 @@ KERNEL_FILES = {8: "dmg_impl.cuh", 16: "dmm16_impl.cuh", 32: "dmm.cu"}
 # summarised in profiles/, keyed by workload, kernel and the kernel source's tag
 # (source_tag) at capture time: a kernel changed since its capture reports null
 NCU_TRAFFIC = {
-    # profiles/dmg_kernel_kitti_1242x375x128.md
-    ("kitti", "dmg_kernel horizontal pass", "dae2685973db"): 300_033_280,
-    ("kitti", "dmg_kernel vertical pass", "dae2685973db"): 232_310_272,
+    # profiles/dmg_kernel_kitti_1242x375x128.md (the horizontal pass: its two
+    # kernels together)
+    ("kitti", "dmg_kernel horizontal pass", "e7a424585df9"): 317_143_808,
+    ("kitti", "dmg_kernel vertical pass", "e7a424585df9"): 245_006_848,
     # dram__bytes.sum.per_second x gpu__time_duration.sum of the capture
     ("minorants", "dmm_alt_kernel horizontal pass", "d05e9b6ae61e"): 3_585_900_000,
     ("minorants", "dmm_alt_kernel vertical pass", "d05e9b6ae61e"): 3_333_000_000,
@@ -509,8 +510,8 @@ NCU_TRAFFIC = {
 # the HBM roofline, against 152 SMs x 4 schedulers x 1 warp-instruction per
 # cycle at 2070 MHz
 NCU_INSTRUCTIONS = {
-    ("kitti", "dmg_kernel horizontal pass", "dae2685973db"): 264_086_625,
-    ("kitti", "dmg_kernel vertical pass", "dae2685973db"): 273_201_498,
+    ("kitti", "dmg_kernel horizontal pass", "e7a424585df9"): 269_208_794,
+    ("kitti", "dmg_kernel vertical pass", "e7a424585df9"): 248_865_750,
 }
 # the refinement kernel (profiles/pd_res_kernel_kitti_1242x375x128.md): warp
 # instructions per launch of 100 iterations, keyed by the source tag of pd.cu

@@ -340,7 +340,7 @@ int run_pass16(dm_ctx* c, int which, uint16_t* labels, long long* lb)
     if (c->use_g) {
         if (c->pool_g) a.pool = reinterpret_cast<int32_t*>(c->ws + c->lay.pool);
         DM_CK(dm::launch_dmg_pass(a, c->gsz, c->radius, c->delta_bytes, c->stream));
-        c->launches += 1;
+        c->launches += dm::dmg_pass_kernels(a, c->gsz);
         return DM_OK;
     }
     DM_CK(dm::launch_dmm16_pass(a, c->np16, c->radius, c->delta_bytes, c->stream));

@@ -322,6 +322,7 @@ cudaError_t launch_dmm16_pass(const Dmm16Args& a, int np, int radius, int delta_
 // (L <= 16 g), 8-bit messages at fmsg/bmsg ([chains][n][16 g] bytes) with int32
 // offsets at fofs/bofs
 cudaError_t launch_dmg_pass(const Dmm16Args& a, int g, int radius, int delta_bytes, cudaStream_t s);
+int dmg_pass_kernels(const Dmm16Args& a, int g);
 // persistent lane-group pass over the chains of many pairs of one label class (G lanes per group)
 cudaError_t launch_dmg_batch(const Batch16Args& b, int g, int radius, int delta_bytes, cudaStream_t s);
 cudaError_t launch_validate_edges(const uint8_t* wh, const uint8_t* wv, int H, int W,

@@ -136,6 +136,18 @@ cudaError_t launch_dmg_pass(const Dmm16Args& a, int g, int radius, int delta_byt
     }
 }
 
+// kernels one lane-group pass launches: 2 when launch_g splits it (a pool is
+// given, from 128 labels on except the 128-label vertical pass, and the chains
+// reach level KL + 1 with segments of 5 or more nodes; KL = log2 of the groups
+// of an 8-warp CTA), else 1
+int dmg_pass_kernels(const Dmm16Args& a, int g)
+{
+    if (a.pool == nullptr || g < 8 || (g == 8 && a.which == 1)) return 1;
+    const int kl = g == 8 ? 5 : 4;
+    const int n = a.which == 0 ? a.W : a.H;
+    return n > 4 && ((n + (1 << kl) - 1) >> kl) >= 5 ? 2 : 1;
+}
+
 cudaError_t launch_dmg_batch(const Batch16Args& b, int g, int radius, int delta_bytes, cudaStream_t s)
 {
     if (delta_bytes == 1) {
