@@ -156,6 +156,7 @@ struct PdResArgs {
 // launch shape of pd_res_kernel (pd_res_plan)
 struct PdResPlan {
     int nx, ny, RW, RH, K, EW, EH, TR, threads;
+    int NS;                  // the kernel's array stride (>= EW * EH)
     size_t smem;
 };
 

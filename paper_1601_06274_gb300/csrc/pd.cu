@@ -17,6 +17,7 @@
 // data weight a scalar or a per-pixel map.
 
 #include <algorithm>
+#include <type_traits>
 #include <utility>
 
 #include "dm_internal.cuh"
@@ -389,12 +390,16 @@ __global__ void __launch_bounds__(kTX * kTY) pd_run_kernel(const PdRunArgs R)
 
 // --- the whole refinement with the state in shared memory ---------------------
 
-// shared-memory bytes of pd_res_kernel for a stored area of EW x EH pixels:
-// nine float arrays (u, u+, u0, s1, s2, ph, pv, qh, qv) and two weight bytes
-__host__ __device__ constexpr size_t res_smem_bytes(int EW, int EH)
+// shared-memory bytes of pd_res_kernel<NS>: nine float arrays (u twice, u0,
+// s1, s2, ph, pv, qh, qv) and two weight byte arrays of NS entries each
+__host__ __device__ constexpr size_t res_smem_bytes(int NS)
 {
-    return (size_t)EW * EH * (9 * sizeof(float) + 2) + 16;
+    return (size_t)NS * (9 * sizeof(float) + 2) + 16;
 }
+
+// the array strides pd_res_kernel is built for (the planner takes the smallest
+// that holds the stored area)
+constexpr int kResStrides[] = {1024, 2048, 3072, 4608, 5888};
 
 // One CTA per region.  The CTA stores its region R and a margin of K pixels
 // on each side that has a neighbouring region (the area E), and runs an epoch
@@ -408,12 +413,13 @@ __host__ __device__ constexpr size_t res_smem_bytes(int EW, int EH)
 // previous exchange, which a CTA behind by one barrier may be reading.  Every
 // warp of the refinement starts an epoch, whose first act is the
 // linearisation of E.  Results equal pd_tile's bit for bit.
+template <int NS>
 __global__ void pd_res_kernel(const PdResArgs R)
 {
     extern __shared__ float4 res_dyn[];
     __shared__ int s_go;
     const PdArgs& A = R.a;
-    const int W = A.W, H = A.H, K = R.K, EW = R.EW, NE = R.EW * R.EH;
+    const int W = A.W, H = A.H, K = R.K, EW = R.EW;
     const int rxi = blockIdx.x % R.nx, ryi = blockIdx.x / R.nx;
     const int x0 = rxi * R.RW, y0 = ryi * R.RH;
     const int w_eff = min(R.RW, W - x0), h_eff = min(R.RH, H - y0);
@@ -426,17 +432,20 @@ __global__ void pd_res_kernel(const PdResArgs R)
     const int shL = ex0 > 0, shR = ex1 < W, shU = ey0 > 0, shD = ey1 < H;
     // region R inside E
     const int rx0 = x0 - ex0, ry0 = y0 - ey0;
-    float* su = reinterpret_cast<float*>(res_dyn);
-    float* sun = su + NE;
-    float* const su0 = sun + NE;
-    float* const ss1 = su0 + NE;
-    float* const ss2 = ss1 + NE;
-    float* const sph = ss2 + NE;
-    float* const spv = sph + NE;
-    float* const sqh = spv + NE;
-    float* const sqv = sqh + NE;
-    uint8_t* const swh = reinterpret_cast<uint8_t*>(sqv + NE);
-    uint8_t* const swv = swh + NE;
+    // arrays of NS entries (NS >= EW * EH, a compile-time stride: every access
+    // is one address plus a constant offset): the two u buffers, u0, s1, s2, the
+    // duals, then the weights as bytes; cur says which u buffer is current
+    float* const sb = reinterpret_cast<float*>(res_dyn);
+    float* const su0 = sb + 2 * NS;
+    float* const ss1 = sb + 3 * NS;
+    float* const ss2 = sb + 4 * NS;
+    float* const sph = sb + 5 * NS;
+    float* const spv = sb + 6 * NS;
+    float* const sqh = sb + 7 * NS;
+    float* const sqv = sb + 8 * NS;
+    uint8_t* const swh = reinterpret_cast<uint8_t*>(sb + 9 * NS);
+    uint8_t* const swv = swh + NS;
+    int cur = 0;
     const int TR = R.TR;
     const int tx = threadIdx.x % EW, ty = threadIdx.x / EW;
     const bool on = (int)threadIdx.x < EW * TR;
@@ -452,7 +461,7 @@ __global__ void pd_res_kernel(const PdResArgs R)
     if (on && tx < ew)
         for (int ey = ty; ey < eh; ey += TR) {
             const int p = ey * EW + tx, i = (ey0 + ey) * W + ex0 + tx;
-            su[p] = R.labels != nullptr ? (float)R.labels[i] : A.u[i];
+            sb[p] = R.labels != nullptr ? (float)R.labels[i] : A.u[i];
             sph[p] = spv[p] = sqh[p] = sqv[p] = 0.0f;
             swh[p] = A.wh[i];
             swv[p] = A.wv[i];
@@ -468,6 +477,7 @@ __global__ void pd_res_kernel(const PdResArgs R)
         const int nit = base + (w < extra ? 1 : 0);
         for (int done = 0; done < nit;) {
             const int steps = min(K, nit - done);
+            float* const su = sb + cur * NS;   // the current u
             if (!first) {
                 // exchange: R's K-wide border out, barrier, the margins of E in
                 const int sp = nex & 1;
@@ -515,7 +525,11 @@ __global__ void pd_res_kernel(const PdResArgs R)
                     }
                 __syncthreads();
             }
-            for (int t = 1; t <= steps; ++t) {
+            // one step with the u buffers at constant offsets (CU: the current one)
+            auto step = [&](auto cu_c, int t) {
+                constexpr int CU = decltype(cu_c)::value;
+                const float* const su = sb + CU * NS;
+                float* const sun = sb + (1 - CU) * NS;
                 // u+ on E less t (left, upper) and t - 1 (right, lower)
                 {
                     const int xa = shL * t, xb = ew - shR * (t - 1);
@@ -562,9 +576,11 @@ __global__ void pd_res_kernel(const PdResArgs R)
                         }
                 }
                 __syncthreads();
-                float* const tmp = su;
-                su = sun;
-                sun = tmp;
+            };
+            for (int t = 1; t <= steps; ++t) {
+                if (cur == 0) step(std::integral_constant<int, 0>{}, t);
+                else step(std::integral_constant<int, 1>{}, t);
+                cur ^= 1;
             }
             done += steps;
         }
@@ -577,6 +593,7 @@ __global__ void pd_res_kernel(const PdResArgs R)
         if (!grid_barrier(R.bar, R.err, R.wait_skew, R.wait_ns, ++nbar, &s_go)) return;
     const int fs = nex & 1;
     const bool lin = R.iters > 0;
+    const float* const su = sb + cur * NS;
     if (on && tx >= rx0 && tx < rx0 + w_eff)
         for (int ey = ry0 + ty; ey < ry0 + h_eff; ey += TR) {
             const int p = ey * EW + tx, i = (ey0 + ey) * W + ex0 + tx;
@@ -1169,7 +1186,14 @@ bool pd_res_plan(int H, int W, PdResPlan* plan)
     plan->EW = plan->RW + (plan->nx > 1 ? 2 * K : 0);
     plan->EH = plan->RH + (plan->ny > 1 ? 2 * K : 0);
     if (plan->EW > 1024) return false;
-    plan->smem = res_smem_bytes(plan->EW, plan->EH);
+    plan->NS = 0;
+    for (const int ns : kResStrides)
+        if (ns >= plan->EW * plan->EH) {
+            plan->NS = ns;
+            break;
+        }
+    if (plan->NS == 0) return false;
+    plan->smem = res_smem_bytes(plan->NS);
     if (plan->smem > (size_t)max_smem) return false;
     plan->TR = std::min(plan->EH, 1024 / plan->EW);
     plan->threads = (plan->EW * plan->TR + 31) / 32 * 32;
@@ -1187,12 +1211,13 @@ int pd_res_result_set(int iters, int warps, int K)
     return epochs > 1 ? (epochs - 1) & 1 : 0;
 }
 
-cudaError_t launch_pd_res(const PdResArgs& r, const PdResPlan& plan, cudaStream_t s)
+template <int NS>
+cudaError_t launch_pd_res_t(const PdResArgs& r, const PdResPlan& plan, cudaStream_t s)
 {
     static size_t smem_set = 0;   // the opt-in is raised once per larger size
     if (plan.smem > smem_set) {
         const cudaError_t e = cudaFuncSetAttribute(
-            pd_res_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+            pd_res_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
         if (e != cudaSuccess) return e;
         smem_set = plan.smem;
     }
@@ -1206,7 +1231,19 @@ cudaError_t launch_pd_res(const PdResArgs& r, const PdResPlan& plan, cudaStream_
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, pd_res_kernel, r);
+    return cudaLaunchKernelEx(&cfg, pd_res_kernel<NS>, r);
+}
+
+cudaError_t launch_pd_res(const PdResArgs& r, const PdResPlan& plan, cudaStream_t s)
+{
+    switch (plan.NS) {
+        case 1024: return launch_pd_res_t<1024>(r, plan, s);
+        case 2048: return launch_pd_res_t<2048>(r, plan, s);
+        case 3072: return launch_pd_res_t<3072>(r, plan, s);
+        case 4608: return launch_pd_res_t<4608>(r, plan, s);
+        case 5888: return launch_pd_res_t<5888>(r, plan, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int TX, int TY>
