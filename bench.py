@@ -515,7 +515,7 @@ NCU_INSTRUCTIONS = {
 }
 # the refinement kernel (profiles/pd_res_kernel_kitti_1242x375x128.md): warp
 # instructions per launch of 100 iterations, keyed by the source tag of pd.cu
-NCU_PD_INSTRUCTIONS = {("pd_res_kernel", 100, "c590292a4644"): 380_328_117}
+NCU_PD_INSTRUCTIONS = {("pd_res_kernel", 100, "468a4778602a"): 347_755_545}
 ISSUE_PEAK_GINST_S = 152 * 4 * 2.070
 
 
