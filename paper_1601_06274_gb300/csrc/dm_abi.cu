@@ -265,7 +265,6 @@ int check_device_error(dm_ctx* c)
         // cleared once reported: the barriers of the next one-launch
         // refinement give up as soon as they see it
         DM_CK(cudaMemsetAsync(c->ws + c->lay.err, 0, sizeof(int32_t), c->stream));
-        DM_CK(cudaMemsetAsync(c->ws + c->lay.pool, 0, pool_bytes(c), c->stream));
         DM_CK(cudaStreamSynchronize(c->stream));
         return DM_ERR_TIMEOUT;
     }

@@ -1106,7 +1106,7 @@ __device__ __noinline__ void leaf_call(const Dmm16Args* A, const uint32_t* s_tap
 // longest segment among its own groups, which keeps its subtrees consistent
 // because no other warp touches them.
 //
-// phase 0 runs the whole chain (every thread of the CTA).  The pooled pass
+// phase 0 runs the whole chain (every thread of the CTA).  The split pass
 // splits it: phase 1 (every thread) runs the levels down to KL, one level
 // further than phase 0's level-synchronous part, and stops; phase 2 (one warp)
 // walks the depth-first subtrees of that warp's groups from the level-(KL+1)
@@ -1143,7 +1143,7 @@ __device__ __forceinline__ void chain_g(const Dmm16Args& A, const Dmm16Args* s_a
     int round = 0;   // 0, 1: the root; then level = round - 1
     bool dfs = false;
     int sp = 0;      // depth-first stack size (warp-uniform)
-    // the first level walked depth first: KL, or KL + 1 in the pooled pass
+    // the first level walked depth first: KL, or KL + 1 in the split pass
     const int LD = phase == 0 ? KL : KL + 1;
     if (phase != 2) {
         // zero boundary messages at both chain ends
@@ -1215,7 +1215,7 @@ __device__ __forceinline__ void chain_g(const Dmm16Args& A, const Dmm16Args* s_a
                 }
             } else {
                 // from level KL on every group walks its segment's subtree depth
-                // first (in the pooled pass, from level KL + 1, in phase 2)
+                // first (in the split pass, from level KL + 1, in phase 2)
                 if (phase == 1) break;
                 dfs = true;
                 if (level == KL && level_max(n, KL - 1) >= 5) {
