@@ -498,8 +498,8 @@ KERNEL_FILES = {8: "dmg_impl.cuh", 16: "dmm16_impl.cuh", 32: "dmm.cu"}
 NCU_TRAFFIC = {
     # profiles/dmg_kernel_kitti_1242x375x128.md (the horizontal pass: its two
     # kernels together)
-    ("kitti", "dmg_kernel horizontal pass", "e7a424585df9"): 317_143_808,
-    ("kitti", "dmg_kernel vertical pass", "e7a424585df9"): 245_006_848,
+    ("kitti", "dmg_kernel horizontal pass", "8adacfeeba4c"): 317_523_200,
+    ("kitti", "dmg_kernel vertical pass", "8adacfeeba4c"): 245_125_632,
     # dram__bytes.sum.per_second x gpu__time_duration.sum of the capture
     ("minorants", "dmm_alt_kernel horizontal pass", "d05e9b6ae61e"): 3_585_900_000,
     ("minorants", "dmm_alt_kernel vertical pass", "d05e9b6ae61e"): 3_333_000_000,
@@ -510,8 +510,8 @@ NCU_TRAFFIC = {
 # the HBM roofline, against 152 SMs x 4 schedulers x 1 warp-instruction per
 # cycle at 2070 MHz
 NCU_INSTRUCTIONS = {
-    ("kitti", "dmg_kernel horizontal pass", "e7a424585df9"): 269_208_794,
-    ("kitti", "dmg_kernel vertical pass", "e7a424585df9"): 248_865_750,
+    ("kitti", "dmg_kernel horizontal pass", "8adacfeeba4c"): 269_208_794,
+    ("kitti", "dmg_kernel vertical pass", "8adacfeeba4c"): 248_865_750,
 }
 # the refinement kernel (profiles/pd_res_kernel_kitti_1242x375x128.md): warp
 # instructions per launch of 100 iterations, keyed by the source tag of pd.cu
