@@ -614,12 +614,15 @@ __device__ __forceinline__ void sweep(const Dmm16Args& A, const Ctx& C, const ui
         const int s0 = bi * KBY;
         const int steps = min(KBY, maxc - s0);
         const int plain = min(steps, max(0, minc - s0));  // steps every group takes
-        // a step's row and base, and its penalty taps, loaded one step ahead
+        // a step's row and base, and its penalty taps, loaded one step ahead; the
+        // word holding the edge weight two steps ahead, so that the taps lookup
+        // (which indexes by the weight) does not wait on a fresh load
         uint32_t th[NWL];
         read_row<Y>(blk, ln, th);
         int base = *reinterpret_cast<const int*>(blk + Gm::BASE_AT);
         int px = pix0 + pst * s0 - wshift;  // left pixel of the step's edge
         tp = taps_of<R>(s_taps, (int)((*reinterpret_cast<const uint32_t*>(blk + Gm::W_AT) >> (8 * (px & 3))) & 0xffu));
+        uint32_t ww_n = *reinterpret_cast<const uint32_t*>(blk + Gm::W_AT + 4 * min(1, KBY - 1));
         int u = 0;
         int stretches = 0;
 #pragma unroll 1
@@ -643,8 +646,8 @@ __device__ __forceinline__ void sweep(const Dmm16Args& A, const Ctx& C, const ui
                     read_row<Y>(blk + un * Gm::ROW, ln, th);
                     base = *reinterpret_cast<const int*>(blk + Gm::BASE_AT + 4 * un);
                     px += pst;
-                    const uint32_t ww = *reinterpret_cast<const uint32_t*>(blk + Gm::W_AT + 4 * un);
-                    tp = taps_of<R>(s_taps, (int)((ww >> (8 * (px & 3))) & 0xffu));
+                    tp = taps_of<R>(s_taps, (int)((ww_n >> (8 * (px & 3))) & 0xffu));
+                    ww_n = *reinterpret_cast<const uint32_t*>(blk + Gm::W_AT + 4 * min(u + 2, KBY - 1));
                 }
                 msg_core<Y::G, NWL, R>(x, m.v, m.off, tc, ln.q);
             }
