@@ -138,9 +138,17 @@ class Clocks:
             uuid = "GPU-" + str(torch.cuda.get_device_properties(device_index).uuid)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", uuid, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # nvidia-smi takes a few hundred ms to start: wait (at most 3 s) for its
+        # first sample so that the sampling covers the whole timed region
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -498,8 +506,8 @@ KERNEL_FILES = {8: "dmg_impl.cuh", 16: "dmm16_impl.cuh", 32: "dmm.cu"}
 NCU_TRAFFIC = {
     # profiles/dmg_kernel_kitti_1242x375x128.md (the horizontal pass: its two
     # kernels together)
-    ("kitti", "dmg_kernel horizontal pass", "8adacfeeba4c"): 317_523_200,
-    ("kitti", "dmg_kernel vertical pass", "8adacfeeba4c"): 245_125_632,
+    ("kitti", "dmg_kernel horizontal pass", "51e0dbb4b9e3"): 317_615_360,
+    ("kitti", "dmg_kernel vertical pass", "51e0dbb4b9e3"): 245_022_464,
     # dram__bytes.sum.per_second x gpu__time_duration.sum of the capture
     ("minorants", "dmm_alt_kernel horizontal pass", "d05e9b6ae61e"): 3_585_900_000,
     ("minorants", "dmm_alt_kernel vertical pass", "d05e9b6ae61e"): 3_333_000_000,
@@ -510,8 +518,8 @@ NCU_TRAFFIC = {
 # the HBM roofline, against 152 SMs x 4 schedulers x 1 warp-instruction per
 # cycle at 2070 MHz
 NCU_INSTRUCTIONS = {
-    ("kitti", "dmg_kernel horizontal pass", "8adacfeeba4c"): 269_208_794,
-    ("kitti", "dmg_kernel vertical pass", "8adacfeeba4c"): 248_865_750,
+    ("kitti", "dmg_kernel horizontal pass", "51e0dbb4b9e3"): 272_887_919,
+    ("kitti", "dmg_kernel vertical pass", "51e0dbb4b9e3"): 252_160_776,
 }
 # the refinement kernel (profiles/pd_res_kernel_kitti_1242x375x128.md): warp
 # instructions per launch of 100 iterations, keyed by the source tag of pd.cu
