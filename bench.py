@@ -508,9 +508,10 @@ NCU_TRAFFIC = {
     # kernels together)
     ("kitti", "dmg_kernel horizontal pass", "51e0dbb4b9e3"): 317_615_360,
     ("kitti", "dmg_kernel vertical pass", "51e0dbb4b9e3"): 245_022_464,
+    # profiles/dmm_alt_staged_kernel_minorants_1242x375x128.md:
     # dram__bytes.sum.per_second x gpu__time_duration.sum of the capture
-    ("minorants", "dmm_alt_kernel horizontal pass", "d05e9b6ae61e"): 3_585_900_000,
-    ("minorants", "dmm_alt_kernel vertical pass", "d05e9b6ae61e"): 3_333_000_000,
+    ("minorants", "dmm_alt_staged_kernel horizontal pass", "4ac94b722085"): 3_568_100_000,
+    ("minorants", "dmm_alt_staged_kernel vertical pass", "4ac94b722085"): 3_343_700_000,
     ("lr", "lr_check_kernel", "68c80f87cd1d"): 3_732_000,
 }
 # smsp__inst_executed.sum per launch from the same captures: a Dual MM pass is
@@ -968,6 +969,8 @@ def run_lr(args):
 # ---------------------------------------------------------------------------
 
 MIN_METRIC = "Mpixel·labels/s (10 Dual MM iterations, iterative minorant) at 1242×375×128"
+# the alternative minorants' kernel at 128 labels (a multiple of 16: the staged form)
+ALT_KERNEL = "dmm_alt_staged_kernel"
 
 
 def run_minorants(args):
@@ -1002,7 +1005,7 @@ def run_minorants(args):
                          "pass_ms": {"horizontal": round(avg[0], 4),
                                      "vertical": round(avg[1], 4)},
                          "kernel": KERNEL_NAMES[ctx.path()[0]] if kind == "hier" else
-                                   "dmm_alt_kernel"}
+                                   ALT_KERNEL}
     # ---- timed region: K solves of 10 iterations with the iterative minorant
     ctx = ctxs["iterative"]
     for _ in range(args.warmup):
@@ -1064,7 +1067,7 @@ def run_minorants(args):
     achieved = bytes_per[dom] / (dur / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "dmm_alt_kernel " + ("horizontal" if dom == 0 else "vertical") + " pass",
+                "kernel": ALT_KERNEL + " " + ("horizontal" if dom == 0 else "vertical") + " pass",
                 "peak_source": src, "bytes_per_launch": bytes_per[dom]}
     roofline["traffic"] = NCU_TRAFFIC.get(("minorants", roofline["kernel"], source_tag("dmm.cu")))
 

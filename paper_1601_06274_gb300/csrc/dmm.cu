@@ -327,7 +327,9 @@ __global__ void __launch_bounds__(kWarps * 32) dmm_pass_kernel(const DmmArgs A)
 // stores the messages it forms (F or B) for the next pass, which runs the
 // other way.  mu accumulates in lam_out; each node's final visit writes
 // lam_out = mu - lam_in and takes the labels and the bound.  The next node's
-// unaries, stored message and mu are loaded one step ahead.
+// unaries, stored message and mu are loaded one step ahead (dmm_alt_kernel,
+// any L); for L a multiple of 16, dmm_alt_staged_kernel below copies them
+// NS - 1 steps ahead into shared memory.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ int floor_div64(long long a, int d)
@@ -520,13 +522,338 @@ __global__ void __launch_bounds__(32) dmm_alt_kernel(const DmmArgs A)
         atomicAdd(reinterpret_cast<unsigned long long*>(A.lb), (unsigned long long)lb_acc);
 }
 
+// ---------------------------------------------------------------------------
+// Staged form of the alternative minorants (label counts that are multiples of
+// 16).  Same chain, same arithmetic and the same results as dmm_alt_kernel,
+// bit for bit; what changes is how a node's inputs reach the warp.  A chain has
+// one warp and its steps depend on one another, so a load issued one step ahead
+// leaves most of a DRAM round trip exposed at every step.  Here every input of
+// a node -- its lambda_in row, its cost row, the stored message of the other
+// direction, its mu (lambda_out of the previous pass) and the word holding the
+// weight of the edge the sweep leaves it by -- is copied into a ring of NS node
+// slots in shared memory by cp.async, NS - 1 steps ahead, one commit group per
+// step.  Copies are 16 bytes where the rows allow it: lambda rows of LPT int32
+// per lane (L a multiple of LPT, so every chunk is aligned and whole), cost
+// rows of L or 2L bytes in 16-byte chunks (L a multiple of 16).  The edge
+// weight comes with its aligned 4-byte word (the workspace's weight arrays
+// start on 256-byte boundaries, so the word stays inside its array).
+// A step is also cut down to what the chain needs: the node's pixel advances
+// by a constant stride per sweep (32-bit element offsets), a lane's labels are
+// all in or all out (one test per lane, not per label), the form of the
+// rounding floor(gamma m) is chosen once per sweep, and the penalty taps come
+// from a copy of the table in shared memory.  Measured on the 1242x375x128
+// frame with the iterative minorant: a horizontal pass 6.04 -> 1.90 ms (375
+// warps; latency-bound), a vertical pass 1.66 -> 0.72 ms (1242 warps; DRAM at
+// two thirds of its peak: the int32 messages and mu of four sweeps per chain).
+// ---------------------------------------------------------------------------
+
+// BYTES of read-only data of the pass (16-byte pieces bypass L1), or with OWN
+// data this warp wrote earlier in the launch (through L1, which holds the
+// SM's own writes)
+template <int BYTES, bool OWN = false>
+__device__ __forceinline__ void cp_async_n(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 32) {
+        cp_async_n<16, OWN>(smem, gmem);
+        cp_async_n<16, OWN>(static_cast<char*>(smem) + 16, static_cast<const char*>(gmem) + 16);
+    } else if constexpr (BYTES == 16 && !OWN) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES)
+                     : "memory");
+    }
+}
+__device__ __forceinline__ void cp_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// one node slot of the ring: lambda_in row, mu row, other-direction message,
+// cost row (room for uint16), edge-weight word
+template <int LPT>
+struct AltSlot {
+    static constexpr int KP = 32 * LPT;
+    static constexpr int LAM = 0, MU = 4 * KP, OTH = 8 * KP, COST = 12 * KP, WORD = 14 * KP;
+    static constexpr int BYTES = 14 * KP + 16;
+};
+
+template <int LPT>
+constexpr int alt_ring_slots() { return 8; }
+
+template <int LPT>
+constexpr int alt_ring_bytes() { return alt_ring_slots<LPT>() * AltSlot<LPT>::BYTES; }
+
+// One sweep of the staged kernel, fixed for its steps: node k0 + dir t at step
+// t, its pixel P0 + DP t (DP = dir times the pixel stride of the chain), the
+// edge it leaves by at pixel offset EOFF from it (every step but the last of a
+// pass has one; the initial backward sweep stops one node short, so all of its
+// steps do).  Element offsets stay below H W L < 2^31 (dm_create's bound).
+struct AltSweep {
+    const int32_t* obuf;  // stored messages of the other direction (nullptr: none)
+    int k0, dir, P0, DP, EOFF, nedge;  // steps t < nedge have an edge
+    bool with_mu;
+};
+
+// cp.async every input of step t's node into slot `slot`
+template <int LPT, bool PAD>
+__device__ __forceinline__ void alt_issue(const DmmArgs& A, const Chain& ch, const AltSweep& sw, int t,
+                                          unsigned char* slot, int lane, bool lane_in, int cost_chunks)
+{
+    using S = AltSlot<LPT>;
+    const int p = sw.P0 + sw.DP * t;
+    const int eo = p * ch.L + lane * LPT;
+    if (!PAD || lane_in) {
+        cp_async_n<4 * LPT>(slot + S::LAM + lane * 4 * LPT, A.lam_in + eo);
+        if (sw.with_mu) cp_async_n<4 * LPT, true>(slot + S::MU + lane * 4 * LPT, A.lam_out + eo);
+    }
+    if (sw.obuf != nullptr)
+        cp_async_n<4 * LPT, true>(slot + S::OTH + lane * 4 * LPT,
+                                  sw.obuf + (sw.k0 + sw.dir * t) * (32 * LPT) + lane * LPT);
+    if (lane < cost_chunks) {  // 16-byte chunks of the cost row (rows only)
+        const unsigned char* row = A.cost16 != nullptr
+                                       ? reinterpret_cast<const unsigned char*>(A.cost16 + p * ch.L)
+                                       : A.cost + p * ch.L;
+        cp_async_n<16>(slot + S::COST + lane * 16, row + lane * 16);
+    }
+    if (lane == 0 && t < sw.nedge) cp_async_n<4>(slot + S::WORD, A.wedge + ((p + sw.EOFF) & ~3));
+}
+
+// step t's node inputs from its slot: theta = lambda_in (+ cost on rows),
+// padding labels infinite; mu 0 when not staged or past L; the weight (or -1)
+template <int LPT, bool PAD>
+__device__ __forceinline__ void alt_read(const DmmArgs& A, const Chain& ch, const AltSweep& sw, int t,
+                                         const unsigned char* slot, int lane, bool lane_in, int (&lam)[LPT],
+                                         NodeIn<LPT>& nd)
+{
+    using S = AltSlot<LPT>;
+    const int* sl = reinterpret_cast<const int*>(slot + S::LAM) + lane * LPT;
+    const int* sm = reinterpret_cast<const int*>(slot + S::MU) + lane * LPT;
+    const int* so = reinterpret_cast<const int*>(slot + S::OTH) + lane * LPT;
+    const bool in = !PAD || lane_in;  // L is a multiple of LPT: a lane's labels are all in or all out
+#pragma unroll
+    for (int j = 0; j < LPT; ++j) {
+        lam[j] = in ? sl[j] : 0;
+        nd.mu[j] = (sw.with_mu && in) ? sm[j] : 0;
+        nd.other[j] = sw.obuf != nullptr ? so[j] : 0;
+    }
+    if (ch.which == 0) {
+        if (A.cost16 != nullptr) {
+            const uint16_t* c = reinterpret_cast<const uint16_t*>(slot + S::COST) + lane * LPT;
+#pragma unroll
+            for (int j = 0; j < LPT; ++j) nd.th[j] = in ? lam[j] + (int)c[j] : kInf;
+        } else {
+            const unsigned char* c = slot + S::COST + lane * LPT;
+#pragma unroll
+            for (int j = 0; j < LPT; ++j) nd.th[j] = in ? lam[j] + (int)c[j] : kInf;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < LPT; ++j) nd.th[j] = in ? lam[j] : kInf;
+    }
+    if (t < sw.nedge) {
+        const int pe = sw.P0 + sw.DP * t + sw.EOFF;
+        nd.om = (int)((*reinterpret_cast<const uint32_t*>(slot + S::WORD) >> (8 * (pe & 3))) & 0xffu);
+    } else {
+        nd.om = -1;
+    }
+}
+
+// the last visit of a node with lambda_in taken from its slot: what
+// finalise_node does
+template <int LPT, bool PAD>
+__device__ __forceinline__ void alt_finalise(const DmmArgs& A, int pix, int lane, bool lane_in,
+                                             const int (&mu)[LPT], const int (&lam)[LPT], long long& lb_acc)
+{
+    int best = kInf, arg = 0x7fffffff;
+    if (!PAD || lane_in) {
+        int32_t* out = A.lam_out + pix * A.L + lane * LPT;
+#pragma unroll
+        for (int j = 0; j < LPT; ++j) {
+            out[j] = mu[j] - lam[j];
+            if (mu[j] < best) {
+                best = mu[j];
+                arg = lane * LPT + j;
+            }
+        }
+    }
+    if (A.labels != nullptr || A.lb != nullptr) {
+        const int m = __reduce_min_sync(kFull, best);
+        if (A.labels != nullptr) {
+            const int cand = (best == m) ? arg : 0x7fffffff;
+            const int am = __reduce_min_sync(kFull, cand);
+            if (lane == 0) A.labels[pix] = (uint16_t)am;
+        }
+        lb_acc += m;
+    }
+}
+
+// penalty taps of weight om from the CTA's copy of the table (flags a weight
+// without an integer table, as taps_for does)
+__device__ __forceinline__ const int* taps_smem(const DmmArgs& A, const int* s_taps, int om)
+{
+    const int* tap = s_taps + om * kTapW;
+    if (tap[kTapValid] == 0) atomicOr(A.err, kDevErrBadOmega);
+    return tap;
+}
+
+template <int LPT, int R, bool PAD, int KIND>
+__global__ void __launch_bounds__(32) dmm_alt_staged_kernel(const DmmArgs A)
+{
+    constexpr int NS = alt_ring_slots<LPT>();
+    constexpr int KP = 32 * LPT;
+    using S = AltSlot<LPT>;
+    extern __shared__ __align__(16) unsigned char s_ring[];
+    // the taps table in shared memory (a lookup per step in global memory
+    // misses L1 once the streamed rows have evicted the table)
+    __shared__ __align__(16) int s_taps[256 * kTapW];
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < 256 * kTapW / 4; i += 32)
+        reinterpret_cast<int4*>(s_taps)[i] = __ldg(reinterpret_cast<const int4*>(A.taps) + i);
+    __syncwarp();
+    Chain ch;
+    ch.which = A.which;
+    ch.W = A.W;
+    ch.L = A.L;
+    ch.KP = A.KP;
+    ch.n = A.which == 0 ? A.W : A.H;
+    ch.c = blockIdx.x;
+    const int n = ch.n;
+    const int pst = A.which == 0 ? 1 : A.W;           // pixels between chain nodes
+    const int pix0 = A.which == 0 ? ch.c * A.W : ch.c;  // pixel of node 0
+    const bool lane_in = lane * LPT < A.L;
+    const int cost_chunks = A.which == 0 ? A.L * (A.cost16 != nullptr ? 2 : 1) / 16 : 0;
+    int32_t* F = A.fmsg + (size_t)ch.c * n * KP;
+    int32_t* B = A.bmsg + (size_t)ch.c * n * KP;
+    const int passes = KIND == 1 ? 1 : A.max_pass;
+    int msgv[LPT], x[LPT], lam[LPT];
+    long long lb_acc = 0;
+
+    // A sweep of cnt steps; step(t, cur) consumes step t's node inputs.  Before
+    // step t the commit groups of steps 0 .. t are complete (NS - 1 + t groups
+    // committed, at most NS - 2 pending); step t + NS - 1 then goes into the
+    // slot of step t - 1, which every lane has read (the __syncwarp after the
+    // wait).
+    auto run = [&](const AltSweep& sw, int cnt, auto step) {
+#pragma unroll 1
+        for (int t = 0; t < NS - 1; ++t) {
+            if (t < cnt) alt_issue<LPT, PAD>(A, ch, sw, t, s_ring + t * S::BYTES, lane, lane_in, cost_chunks);
+            cp_commit_group();
+        }
+        unsigned char* rd = s_ring;                       // slot of step t
+        unsigned char* wr = s_ring + (NS - 1) * S::BYTES;  // slot of step t + NS - 1
+#pragma unroll 1
+        for (int t = 0; t < cnt; ++t) {
+            cp_wait_group<NS - 2>();
+            __syncwarp();
+            NodeIn<LPT> cur;
+            alt_read<LPT, PAD>(A, ch, sw, t, rd, lane, lane_in, lam, cur);
+            if (t + NS - 1 < cnt) alt_issue<LPT, PAD>(A, ch, sw, t + NS - 1, wr, lane, lane_in, cost_chunks);
+            cp_commit_group();
+            rd = rd + S::BYTES == s_ring + NS * S::BYTES ? s_ring : rd + S::BYTES;
+            wr = wr + S::BYTES == s_ring + NS * S::BYTES ? s_ring : wr + S::BYTES;
+            step(t, cur);
+        }
+        cp_wait_group<0>();
+        __syncwarp();
+    };
+
+    // backward sweep of the chain with mu = 0: B_{k-1} = Msg(theta_k + B_k),
+    // k = n - 1 .. 1, over the edge (k - 1, k)
+#pragma unroll
+    for (int j = 0; j < LPT; ++j) msgv[j] = 0;
+    store_msg<LPT>(B + (size_t)(n - 1) * KP, lane, msgv);
+    {
+        const AltSweep sw{nullptr, n - 1, -1, pix0 + (n - 1) * pst, -pst, -pst, n - 1, false};
+        int32_t* bk = B + (size_t)(n >= 2 ? n - 2 : 0) * KP;  // the message into node k - 1
+        run(sw, n - 1, [&](int t, NodeIn<LPT>& cur) {
+            const int* tap = taps_smem(A, s_taps, cur.om);
+#pragma unroll
+            for (int j = 0; j < LPT; ++j) x[j] = cur.th[j] + msgv[j];
+            msg<LPT, R, PAD>(x, msgv, tap, lane, A.L);
+            store_msg<LPT>(bk, lane, msgv);
+            bk -= KP;
+        });
+    }
+
+#pragma unroll 1
+    for (int s = 1; s <= passes; ++s) {
+        const bool last = s == passes;
+        const bool fwd = (s & 1) == 1;
+        const int num = KIND == 1 ? 1 : (last ? 1 : A.gamma_num);
+        const int den = KIND == 1 ? n : (last ? 1 : A.gamma_den);
+        const int shift = (den & (den - 1)) == 0 ? __ffs(den) - 1 : -1;  // den = 2^shift
+        // the form of floor(m gamma) for the whole sweep: m, m >> shift, 32-bit
+        // or 64-bit division (gamma_part's cases, decided once)
+        const int gform = num == den ? 0 : (num == 1 ? (shift >= 0 ? 1 : 2) : 3);
+        const AltSweep sw{fwd ? B : F, fwd ? 0 : n - 1, fwd ? 1 : -1,
+                          pix0 + (fwd ? 0 : (n - 1) * pst), fwd ? pst : -pst, fwd ? 0 : -pst, n - 1,
+                          s > 1};
+        int32_t* sk = (fwd ? F : B) + (size_t)(fwd ? 0 : n - 1) * KP;  // messages this pass forms
+        const int dk = fwd ? KP : -KP;
+#pragma unroll
+        for (int j = 0; j < LPT; ++j) msgv[j] = 0;
+        run(sw, n, [&](int t, NodeIn<LPT>& cur) {
+            const int pix = sw.P0 + sw.DP * t;
+            const int* tap = cur.om >= 0 ? taps_smem(A, s_taps, cur.om) : nullptr;
+            if (!last) store_msg<LPT>(sk, lane, msgv);
+            sk += dk;
+            int m[LPT];
+#pragma unroll
+            for (int j = 0; j < LPT; ++j) m[j] = msgv[j] + cur.th[j] - cur.mu[j] + cur.other[j];
+            if (!PAD || lane_in) {
+                if (gform == 0) {
+#pragma unroll
+                    for (int j = 0; j < LPT; ++j) cur.mu[j] += m[j];
+                } else if (gform == 1) {
+#pragma unroll
+                    for (int j = 0; j < LPT; ++j) cur.mu[j] += m[j] >> shift;
+                } else if (gform == 2) {
+#pragma unroll
+                    for (int j = 0; j < LPT; ++j) cur.mu[j] += floor_div32(m[j], den);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < LPT; ++j) cur.mu[j] += floor_div64((long long)m[j] * num, den);
+                }
+            }
+            if (last) {
+                alt_finalise<LPT, PAD>(A, pix, lane, lane_in, cur.mu, lam, lb_acc);
+            } else if (!PAD || lane_in) {
+                int32_t* out = A.lam_out + pix * A.L + lane * LPT;
+#pragma unroll
+                for (int j = 0; j < LPT; ++j) out[j] = cur.mu[j];
+            }
+            if (t + 1 < n) {
+                // the naive minorant takes the min-marginals of f itself; the
+                // iterative one those of the remainder f - mu, mu_k just updated
+#pragma unroll
+                for (int j = 0; j < LPT; ++j)
+                    x[j] = cur.th[j] - (KIND == 1 ? 0 : cur.mu[j]) + msgv[j];
+                msg<LPT, R, PAD>(x, msgv, tap, lane, A.L);
+            }
+        });
+    }
+    if (A.lb != nullptr && lane == 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(A.lb), (unsigned long long)lb_acc);
+}
+
 template <int LPT, int R, int KIND>
 void launch_alt(const DmmArgs& a, int chains, cudaStream_t s)
 {
-    if (a.L == 32 * LPT)
+    // label counts that are multiples of 16 (every chunk of a row whole and
+    // aligned) take the staged kernel; the rest the one-step-ahead loads
+    if (a.L % 16 == 0) {
+        if (a.L == 32 * LPT)
+            dmm_alt_staged_kernel<LPT, R, false, KIND><<<chains, 32, alt_ring_bytes<LPT>(), s>>>(a);
+        else
+            dmm_alt_staged_kernel<LPT, R, true, KIND><<<chains, 32, alt_ring_bytes<LPT>(), s>>>(a);
+    } else if (a.L == 32 * LPT) {
         dmm_alt_kernel<LPT, R, false, KIND><<<chains, 32, 0, s>>>(a);
-    else
+    } else {
         dmm_alt_kernel<LPT, R, true, KIND><<<chains, 32, 0, s>>>(a);
+    }
 }
 
 template <int LPT, int R>

@@ -2,7 +2,10 @@
 Fast Minorants"; Alg. iterative-minorant) on the GPU against the int64 oracle:
 both duals after every pass, the labels and the lower bounds bit-exact, on
 ragged shapes and label counts of every register class; sampled chains of the
-1242x375x128 frame against the oracle's per-chain minorant.
+1242x375x128 frame against the oracle's per-chain minorant.  Label counts that
+are multiples of 16 run the staged kernel (inputs copied NS - 1 steps ahead
+into shared memory), the others the kernel with one-step-ahead loads; the
+shapes cover both.
 """
 
 import numpy as np
@@ -130,9 +133,11 @@ def test_full_frame_sampled_chains(dm, kind):
 
 
 @pytest.mark.parametrize("kind", ["naive", "iterative"])
-def test_uint16_cost_storage(dm, kind):
-    """The alternatives read uint16 cost volumes too: the same numbers as uint8."""
-    H, W, L = 11, 23, 40
+@pytest.mark.parametrize("L", [40, 48, 128])
+def test_uint16_cost_storage(dm, kind, L):
+    """The alternatives read uint16 cost volumes too: the same numbers as uint8
+    (L = 40 on the one-step-ahead kernel, 48 and 128 on the staged one)."""
+    H, W = 11, 23
     sp = S.make_pair(H, W, L, planes=3, noise_sigma=2.0, seed=77)
     ctx = dm.Context(H, W, L, dm.default_params(cost_bytes=2))
     ctx.cost_volume(sp.left, sp.right)
