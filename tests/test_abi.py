@@ -262,3 +262,29 @@ def test_capture_and_replay_check_state_without_gpu(lib):
     assert lib.dm_replay(h) == dm.DM_ERR_STATE
     assert lib.dm_replay(None) == dm.DM_ERR_ARG
     lib.dm_destroy(h)
+
+
+def test_noalloc_checks_arguments_without_gpu(lib):
+    """dm_discrete_pass_noalloc refuses bad calls in host code, before it looks up
+    its scratch array or launches anything (the pointers here are never used)."""
+    from paper_1601_06274_gb300 import dm
+    p = dm.default_params()
+    lam_in, lam_out, err = ctypes.c_void_p(4096), ctypes.c_void_p(8192), ctypes.c_void_p(12288)
+
+    def call(H, W, L, params, which, cost, lin, lout, e):
+        pp = ctypes.byref(params) if params is not None else None
+        return lib.dm_discrete_pass_noalloc(H, W, L, pp, which, cost, lam_in, lin, lout, e, None)
+
+    # two int32 message arrays of 256 * 256 nodes * 128 labels: 64 MiB > 32 MiB of scratch
+    assert call(256, 256, 128, p, 0, lam_in, lam_in, lam_out, err) == dm.DM_ERR_WORKSPACE
+    assert call(8, 8, 16, None, 0, lam_in, lam_in, lam_out, err) == dm.DM_ERR_ARG
+    assert call(8, 8, 16, p, 2, lam_in, lam_in, lam_out, err) == dm.DM_ERR_ARG        # which
+    assert call(8, 8, 16, p, 0, None, lam_in, lam_out, err) == dm.DM_ERR_ARG         # rows need costs
+    assert call(8, 8, 16, p, 0, lam_in, lam_in, lam_in, err) == dm.DM_ERR_ARG        # aliased output
+    assert call(8, 8, 16, p, 0, lam_in, lam_in, lam_out, None) == dm.DM_ERR_ARG      # no error word
+    assert call(0, 8, 16, p, 0, lam_in, lam_in, lam_out, err) == dm.DM_ERR_ARG
+    assert call(8, 8, 1, p, 0, lam_in, lam_in, lam_out, err) == dm.DM_ERR_ARG
+    assert call(8, 8, 257, p, 0, lam_in, lam_in, lam_out, err) == dm.DM_ERR_ARG
+    for bad in (dm.default_params(w_hi=3), dm.default_params(tau=-1.0),
+                dm.default_params(struct_size=8)):
+        assert call(8, 8, 16, bad, 0, lam_in, lam_in, lam_out, err) == dm.DM_ERR_ARG
